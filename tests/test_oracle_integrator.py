@@ -1,0 +1,124 @@
+"""Pins for the oracle's KDK integrator (Eq. 9-11), RK4 scale factor (Eq. 1),
+the comoving equation of motion (Eq. 8) and the pair counts.
+
+Pins: Kepler's period and second-order convergence of KDK, energy conservation
+in a static background, the flat-LambdaCDM closed form a(t), a uniform
+comoving sphere that must feel no peculiar acceleration, and pair counts from
+an independent k-d tree.
+"""
+import math
+
+import numpy as np
+import pytest
+from scipy.spatial import cKDTree
+
+import oracle
+from paper_1811_05903_gb300 import workloads
+
+
+def kepler(e, dt, periods):
+    """Two equal masses, G = M = 1, semi-major axis 1, released at apocentre."""
+    ra = 1.0 + e
+    vrel = math.sqrt((1.0 - e) / (1.0 + e))
+    pos = np.array([[0.5 * ra, 0, 0], [-0.5 * ra, 0, 0]])
+    vel = np.array([[0, 0.5 * vrel, 0], [0, -0.5 * vrel, 0]])
+    m = np.array([0.5, 0.5])
+    h = np.array([1e-4, 1e-4])
+    kd = oracle.KDK(pos, vel, m, h, oracle.cosmo(comoving=False))
+    e0 = kd.energy()
+    nsteps = int(round(periods * 2 * math.pi / dt))
+    de_max = 0.0
+    for _ in range(nsteps):
+        kd.step(dt)
+        de_max = max(de_max, abs(kd.energy() - e0) / abs(e0))
+    return kd, de_max, pos
+
+
+@pytest.mark.parametrize("e", [0.0, 0.5])
+def test_kepler_period_and_second_order(e):
+    errs = []
+    for dt in (2 * math.pi / 400, 2 * math.pi / 800):
+        kd, de, pos0 = kepler(e, dt, 10)
+        # after whole periods the bodies are back at the start (period 2 pi sqrt(a^3/GM))
+        dx = np.linalg.norm(kd.pos - pos0)
+        errs.append((de, dx))
+    (de1, dx1), (de2, dx2) = errs
+    assert dx1 < 0.2 and dx2 < dx1
+    # second order: halving dt cuts the phase error and the (bounded, oscillating)
+    # energy error ~4x; on a circular orbit the energy error is at rounding level
+    assert 3.0 < dx1 / dx2 < 5.0
+    if e > 0:
+        assert 3.0 < de1 / de2 < 5.0
+    assert de2 < 1e-3
+
+
+def test_static_energy_conservation_small_system():
+    p = workloads.static_ball(seed=1)
+    h = oracle.softening(p.mass, p.h_min)
+    des = []
+    for dt in (1e-3, 5e-4):
+        kd = oracle.KDK(p.pos, p.vel, p.mass, h, oracle.cosmo(comoving=False))
+        e0 = kd.energy()
+        for _ in range(int(round(0.01 / dt))):
+            kd.step(dt)
+        des.append(abs(kd.energy() - e0) / abs(e0))
+        # momentum stays zero in the static mode (Newton's third law)
+        _, pmom = oracle.kinetic(kd.vel, kd.m)
+        assert np.linalg.norm(pmom) < 1e-11 * (kd.m.sum() * np.abs(kd.vel).max() + 1e-300) + 1e-12
+    # the heavy outer shells dominate E; at dt = 1e-3 the drift is ~2e-4 and
+    # falls as dt^2 (KDK is second order)
+    assert des[0] < 1e-3
+    assert 3.5 < des[0] / des[1] < 4.5
+
+
+def test_rk4_matches_flat_lcdm_closed_form():
+    c = oracle.cosmo(Om=0.3, OL=0.7, comoving=True)
+    a_sched, dts = workloads.loga_schedule(0.02, 1.0, 200, 0.3, 0.7)
+    a = a_sched[0]
+    for n, dt in enumerate(dts):
+        a = oracle.rk4_a(a, dt, c)
+        assert abs(a - a_sched[n + 1]) <= 1e-9 * a_sched[n + 1]
+    # Eq. 1 itself: H(a=1) = H0 and the matter era limit
+    assert math.isclose(oracle.hubble(1.0, c), 1.0, rel_tol=1e-15)
+    assert math.isclose(oracle.hubble(0.5, c), math.sqrt(0.3 * 8 + 0.7), rel_tol=1e-15)
+
+
+def test_uniform_comoving_sphere_has_no_peculiar_acceleration():
+    """Eq. 8 with the background term (4 pi G/3) rho_bar x / a^3: inside a
+    uniform sphere of mean density rho_bar the pair sum and the background
+    cancel at any a.  A sign error gives a ratio near 2, a missing 1/a^3 a
+    ratio near 1 - a^-3."""
+    rng = np.random.default_rng(5)
+    n, R, Om = 16384, 10.0, 0.3
+    rho = Om * 3 / (8 * math.pi)
+    pos = rng.uniform(-1, 1, (4 * n, 3))
+    pos = pos[(pos ** 2).sum(1) <= 1][:n] * R
+    m = np.full(n, rho * 4 / 3 * math.pi * R ** 3 / n)
+    h = np.full(n, 1e-3)
+    a = 0.5
+    c = oracle.cosmo(Om=Om, OL=1 - Om, comoving=True)
+    kd = oracle.KDK(pos, np.zeros_like(pos), m, h, c, a0=a)
+    dt = 1e-7
+    kd.step(dt)
+    A = kd.vel / dt  # ~ the Eq. 8 acceleration at rest
+    r = np.linalg.norm(pos, axis=1)
+    inner = r < 0.5 * R
+    ar = (A[inner] * pos[inner]).sum(1) / r[inner]
+    bg = 4 * math.pi / 3 * rho * r[inner] / a ** 3
+    ratio = ar.mean() / bg.mean()
+    assert abs(ratio) < 0.05, ratio
+
+
+def test_paircount_matches_kdtree():
+    rng = np.random.default_rng(9)
+    n = 1500
+    scale = 2 ** 16
+    q = rng.integers(-scale, scale, size=(n, 3)).astype(np.int32)
+    # squared edges in integer units, log spaced
+    edges = np.geomspace(2000.0, 60000.0, 13)
+    edge2 = np.ceil(edges ** 2).astype(np.int64)
+    dd = oracle.paircount(q, edge2)
+    tree = cKDTree(q.astype(np.float64))
+    # an integer d^2 < E  <=>  d <= sqrt(E - 1/2); no integer distance sits on that radius
+    cum = np.array([(tree.count_neighbors(tree, math.sqrt(E - 0.5)) - n) // 2 for E in edge2])
+    np.testing.assert_array_equal(dd.astype(np.int64), np.diff(cum))
