@@ -1,0 +1,349 @@
+"""Benchmark: pair interactions/s of the StePS direct-summation step on GB300.
+
+Workload (default): the N = 2^20 compactified precision-study set (524,288
+central particles in 50 Mpc/h + 64 shells x 8,192 out to 4,000 Mpc/h),
+comoving LambdaCDM, FP32 pair arithmetic with tile-relative coordinates and
+compensated sums, FP64 integrator.  One step = one full kick-drift-kick step
+(kick, drift, RK4 a(t), staging, pair-force kernel, fixup, kick; spatial
+re-sort every 8 steps), i.e. N^2 pair interactions.
+
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+Multi-GPU (torchrun): the path does not shard; each rank runs an independent
+replica and the job value is the sum of all ranks' interactions over the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "pair interactions/s at N=2^20: mixed vs FP64 GPU at <=1e-6 rms rel force err"
+UNIT = "interactions/s"
+FLOP_PER_INTERACTION = 20  # the usual direct N-body convention
+L2_FLUSH_BYTES = 512 << 20
+
+
+def peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def fp32_peak_tflops(sm_count: int, sm_mhz: float) -> float:
+    """FP32 FMA peak: SMs x 128 lanes x 2 flop x clock."""
+    return sm_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+
+
+class ClockSampler:
+    """nvidia-smi clocks/throttle sampling during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.file, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.flush()
+        rows = []
+        with open(self.file.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append((float(parts[1]), float(parts[2]), parts[4:9]))
+                except ValueError:
+                    continue
+        os.unlink(self.file.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for _, _, r in rows:
+            for nm, v in zip(names, r[1:]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(r[0] for r in rows), "sm_max_mhz": max(r[1] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def build_workload(name: str):
+    from paper_1811_05903_gb300 import workloads
+    if name == "precision_1m":
+        return workloads.precision_1m(), "StePS compactified LCDM, N=1,048,576 (524,288 central in 50 Mpc/h + 64 shells x 8,192 to 4,000 Mpc/h), a=0.02"
+    if name == "lcdm_262k":
+        return workloads.lcdm_262k(), "StePS compactified LCDM, N=262,144 (131,072 central + 64 shells x 2,048), a=0.02"
+    raise SystemExit("unknown workload " + name)
+
+
+def run_reference(args):
+    """The FP64 CPU oracle on a bounded sample of the same workload."""
+    import oracle
+    from paper_1811_05903_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    oracle.build()
+    p, desc = build_workload(args.workload)
+    h = oracle.softening(p.mass, p.h_min)
+    nt = args.ref_targets
+    rng = np.random.default_rng(12345)
+    for _ in range(args.warmup):
+        oracle.pair_acc(p.pos, p.mass, h, p.G, targets=np.sort(rng.choice(p.n, nt, replace=False)))
+    times = []
+    for _ in range(args.steps):
+        tg = np.sort(rng.choice(p.n, nt, replace=False))
+        t0 = time.perf_counter()
+        oracle.pair_acc(p.pos, p.mass, h, p.G, targets=tg)
+        times.append(time.perf_counter() - t0)
+    value = args.steps * nt * p.n / sum(times)
+    cores = os.cpu_count()
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": desc, "n": p.n, "sample_targets": nt},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": "%d seeded targets x all %d sources per step (FP64 direct sum, OpenMP)" % (nt, p.n)},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_1811_05903_gb300.build as libbuild
+    from paper_1811_05903_gb300 import steps, workloads
+
+    ws, rank, local = dist_env()
+    if ws > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    libbuild.build()
+    steps.load()
+    dev = torch.device("cuda", local)
+    props = torch.cuda.get_device_properties(dev)
+
+    p, desc = build_workload(args.workload)
+    n = p.n
+    a_sched, dts = workloads.loga_schedule(p.a0, 1.0, 200, p.Om, p.OL)
+    stream = torch.cuda.Stream(device=dev)
+    cfg = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_COMP, G=p.G, Om=p.Om, OL=p.OL,
+                            resort_every=8, tile_override=args.variant)
+    sim = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg,
+                           stream=stream.cuda_stream)
+    flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # ---- accuracy at the initial positions (mixed, naive, FP64 GPU) ----
+    acc_mixed = np.empty((n, 3))
+    steps.steps_get_state(sim.ctx, acc=acc_mixed)
+    tg = workloads.precision_targets(n)
+    acc64 = steps.steps_forces_subset(sim.ctx, tg)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    big_tg = np.sort(np.random.default_rng(7).choice(n, min(n, args.f64_targets), replace=False))
+    with torch.cuda.stream(stream):
+        ev0.record(stream)
+    steps.steps_forces_subset(sim.ctx, big_tg)
+    with torch.cuda.stream(stream):
+        ev1.record(stream)
+    ev1.synchronize()
+    f64_ms = ev0.elapsed_time(ev1)
+    f64_rate = big_tg.size * n / (f64_ms * 1e-3)
+
+    cfg_naive = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_NAIVE, G=p.G, Om=p.Om,
+                                  OL=p.OL)
+    naive = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg_naive,
+                             stream=stream.cuda_stream)
+    acc_naive = np.empty((n, 3))
+    steps.steps_get_state(naive.ctx, acc=acc_naive)
+    steps.steps_profile_enable(naive.ctx, True)
+    for _ in range(2):
+        steps.steps_forces(naive.ctx)
+    naive_ms, naive_launches, _ = steps.steps_profile_read(naive.ctx)
+    naive_rate = naive_launches * n * n / (naive_ms * 1e-3)
+    naive.close()
+
+    # ---- CPU baseline: the FP64 oracle on the seeded targets (rank 0 only) ----
+    cpu = None
+    err = {}
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        h = oracle.softening(p.mass, p.h_min)
+        t0 = time.perf_counter()
+        ref = oracle.pair_acc(p.pos, p.mass, h, p.G, targets=tg)
+        cpu_s = time.perf_counter() - t0
+        cpu = {"value": tg.size * n / cpu_s, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+               "sample": "%d seeded targets x all %d sources (FP64 direct sum, OpenMP), %.1f s" % (tg.size, n, cpu_s)}
+        nrm = np.linalg.norm(ref, axis=1)
+        for name, a in (("f32_comp", acc_mixed[tg]), ("f32_naive", acc_naive[tg]), ("f64_gpu", acc64)):
+            e = np.linalg.norm(a - ref, axis=1) / nrm
+            err[name] = {"rms": float(np.sqrt(np.mean(e ** 2))), "max": float(e.max())}
+
+    # ---- warm-up and timed KDK steps ----
+    for k in range(args.warmup):
+        sim.step(dts[k])
+    torch.cuda.synchronize()
+    steps.steps_profile_read(sim.ctx, reset=True)
+    steps.steps_profile_enable(sim.ctx, True)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        wall0 = time.perf_counter()
+        for k in range(args.steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()                      # L2 flush between timed steps (not timed)
+                starts[k].record(stream)
+            sim.step(dts[args.warmup + k])
+            with torch.cuda.stream(stream):
+                ends[k].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - wall0
+    if ws > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    force_ms, force_launches, kernel_launches = steps.steps_profile_read(sim.ctx, reset=True)
+    steps.steps_profile_enable(sim.ctx, False)
+    total_s = sum(step_ms) * 1e-3
+    if ws > 1:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_s = float(t.item())
+    interactions = args.steps * n * n * ws
+    value = interactions / total_s
+
+    # ---- end to end through the C ABI with host buffers ----
+    pos_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    vel_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    acc_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
+    t_now, a_now = steps.steps_get_state(sim.ctx, pos=pos_h.numpy(), vel=vel_h.numpy())
+    steps.steps_set_state(sim.ctx, pos_h.numpy(), vel_h.numpy(), t_now, a_now)  # warm
+    torch.cuda.synchronize()
+    e2e_steps = max(1, min(args.steps, 3))
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        steps.steps_set_state(sim.ctx, pos_h.numpy(), vel_h.numpy(), t_now, a_now)  # H2D + sort + forces
+        steps.steps_get_state(sim.ctx, acc=acc_h.numpy())                         # D2H of the result
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": e2e_steps * n * n * ws / e2e_s, "unit": UNIT,
+           "h2d_bytes_per_step": 2 * 3 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n,
+           "what": "steps_set_state(host pos, vel) + steps_get_state(host acc): one force evaluation per step"}
+    sim.close()
+
+    if rank != 0:
+        dist.destroy_process_group()
+        return
+    clocks = clk.summary()
+    force_avg_s = force_ms * 1e-3 / max(force_launches, 1)
+    achieved = FLOP_PER_INTERACTION * n * n / force_avg_s / 1e12
+    pk = peaks()
+    max_mhz = float(pk.get("sm_max_mhz", 2070.0))
+    peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": desc, "n": n, "prec": "f32 pairs, compensated sums, fp64 integrator",
+                   "parallelism": "replicas" if ws > 1 else "single gpu",
+                   "l2": "flushed between timed steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20),
+                   "variant": args.variant or "auto"},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "kernel": "force_f32_kernel (pair forces)",
+                     "basis": "%d flop/interaction x N^2 per launch / mean launch time; peak = %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
+                              % (FLOP_PER_INTERACTION, props.multi_processor_count, max_mhz),
+                     "frac_at_observed_clock": (achieved / fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
+                                                if clocks.get("sm_mhz") else None)},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "clocks": clocks,
+        "gpu_launches": int(kernel_launches),
+        "comparison": {
+            "f32_comp": {"interactions_per_s": value / ws, "force_kernel_interactions_per_s": n * n / force_avg_s,
+                         **err.get("f32_comp", {})},
+            "f32_naive": {"force_kernel_interactions_per_s": naive_rate, **err.get("f32_naive", {})},
+            "f64_gpu": {"interactions_per_s": f64_rate, "sample": "%d targets x %d sources" % (big_tg.size, n),
+                        **err.get("f64_gpu", {})},
+            "error_targets": int(tg.size),
+        },
+        "wall_s_timed": wall,
+    }
+    print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=8)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="precision_1m")
+    ap.add_argument("--variant", type=int, default=0, help="force-kernel variant (1-based), 0 = auto")
+    ap.add_argument("--f64-targets", type=int, default=16384)
+    ap.add_argument("--ref-targets", type=int, default=512)
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

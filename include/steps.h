@@ -1,0 +1,213 @@
+/*
+ * steps.h -- C ABI of libsteps, a GB300 (sm_103a) direct-summation gravity
+ * engine for StePS-style compactified N-body simulations (Racz, Szapudi,
+ * Dobos, Csabai & Szalay, "StePS: A Multi-GPU Cosmological N-body Code for
+ * Compactified Simulations").
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units are the caller's; G is taken from steps_config.  H0 and time share
+ *    one unit (the Friedmann equation, Eq. 1, is evaluated as written).
+ *  - Arrays of 3-vectors are row-major [n][3] float64.  Scalars are float64.
+ *  - Any array argument may be a host pointer or a device pointer on the
+ *    context's device; the library classifies it with cudaPointerGetAttributes
+ *    and copies as needed.  The caller keeps ownership of every buffer it
+ *    passes; the library copies inputs before the call returns.
+ *  - Particle order at the boundary is always the caller's order.  The
+ *    library keeps its state spatially sorted internally; the permutation
+ *    never leaks.
+ *  - Every entry point returns a steps_status and never aborts.  On failure
+ *    steps_last_error() returns a thread-local, human-readable reason.
+ *  - Work is issued on the stream given at steps_init.  With NULL the context
+ *    creates and owns a private non-blocking stream.  Calls that return data
+ *    (forces, state, diagnostics, checkpoints) synchronise that stream before
+ *    returning; steps_kdk_step without a_out and steps_kdk_run's graph
+ *    replays are asynchronous until the next synchronising call.
+ */
+#ifndef STEPS_H
+#define STEPS_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STEPS_OK = 0,
+    STEPS_EINVAL = 1,       /* bad argument: NULL where required, n <= 0, non-finite input, h <= 0 */
+    STEPS_ENOMEM = 2,       /* device allocation failed or exceeds the context's cap */
+    STEPS_ECUDA = 3,        /* a CUDA runtime call failed; see steps_last_error() */
+    STEPS_ETIMEOUT = 4,     /* a bounded device-side wait ran out; the kernel exited cleanly */
+    STEPS_ENONFINITE = 5,   /* a result contained NaN or Inf */
+    STEPS_EUNSUPPORTED = 6  /* option not built into this library */
+} steps_status;
+
+typedef enum {
+    STEPS_STATIC = 0,   /* static, non-comoving Newtonian background (the paper's proper-coordinate mode) */
+    STEPS_COMOVING = 1  /* spherical comoving equation of motion, Eq. 8 */
+} steps_mode;
+
+typedef enum {
+    STEPS_F32_COMP = 0,  /* FP32 pair arithmetic, tile-relative coordinates, compensated per-target sums */
+    STEPS_F32_NAIVE = 1, /* FP32 pair arithmetic, one plain FP32 running sum per target */
+    STEPS_F64 = 2        /* FP64 pair arithmetic and sums on the GPU */
+} steps_prec;
+
+typedef struct {
+    double G;                 /* gravitational constant */
+    double H0;                /* Hubble constant (1/time unit) */
+    double Om, OL, Or, Ok;    /* density parameters of Eq. 1 (present-day values) */
+    int mode;                 /* steps_mode */
+    int prec;                 /* steps_prec */
+    int resort_every;         /* re-sort particles spatially every this many steps (<=0: default 8) */
+    int tile_override;        /* 0 = autotuned force-kernel variant; k>0 selects variant k-1 */
+} steps_config;
+
+typedef struct steps_ctx steps_ctx;
+
+/* Default configuration: G = H0 = 1, Om = 0.3, OL = 0.7, static mode, STEPS_F32_COMP. */
+steps_config steps_default_config(void);
+
+/*
+ * steps_init -- create a simulation context holding n particles on the
+ * current CUDA device.
+ *   pos  [n][3]  positions (comoving in STEPS_COMOVING mode)
+ *   vel  [n][3]  velocities dx/dt (NULL = zero)
+ *   mass [n]     particle masses, > 0
+ *   soft [n]     per-particle softening lengths h_i (> 0), or NULL to derive
+ *                them from the masses by Eq. 7, h_i = (m_i/m_min)^(1/3) h_min
+ *   h_min        softening of the lightest particle; used only when soft == NULL
+ *   t0, a0       initial cosmic time and scale factor (a0 ignored in static mode)
+ *   cfg          configuration (NULL = steps_default_config())
+ *   cuda_stream  cudaStream_t to issue work on (NULL = a private stream)
+ * Each pair (i, j) uses the softening support h_i + h_j (Eq. 2, Eq. 8).
+ * The pair term at the initial positions is computed before returning.
+ * Errors: EINVAL (n <= 0, NULL pos/mass/out, non-finite values, m <= 0,
+ * h <= 0), ENOMEM, ECUDA.  On error *out is set to NULL.
+ */
+steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const double *vel,
+                        const double *mass, const double *soft, double h_min, double t0,
+                        double a0, const steps_config *cfg, void *cuda_stream);
+
+/*
+ * steps_forces -- evaluate the softened pair term of Eq. 8 at the current
+ * positions (Eq. 3 with the spline kernel of Eq. 4, summed over all j != i):
+ *   acc_i = -G sum_{j != i} m_j F(|x_i - x_j|, h_i + h_j) (x_i - x_j)/|x_i - x_j|
+ * i.e. the pair acceleration before the 1/a^3 factor, in the precision chosen
+ * by cfg.prec.  acc_out [n][3] (host or device, caller order) may be NULL, in
+ * which case the result only refreshes the context's stored acceleration.
+ */
+steps_status steps_forces(steps_ctx *ctx, double *acc_out);
+
+/*
+ * steps_kdk_step -- advance one kick-drift-kick step of length dt
+ * (Eq. 9-11, one force evaluation per step).  In STEPS_COMOVING mode each
+ * half-kick applies A = acc/a^3 - 2 (adot/a) v + (4 pi G/3) Om rho_crit x / a^3
+ * (Eq. 8; rho_crit = 3 H0^2/(8 pi G)), with a and adot/a taken at that
+ * half-kick's time point and v at kick entry; a(t) advances by one RK4 step
+ * of Eq. 1 with the same dt.  In STEPS_STATIC mode A = acc.
+ * a_out (host, may be NULL) receives the new scale factor; passing it
+ * synchronises the stream.  All state stays on the device (FP64).
+ */
+steps_status steps_kdk_step(steps_ctx *ctx, double dt, double *a_out);
+
+/*
+ * steps_kdk_run -- nsteps KDK steps with per-step lengths dts[nsteps] (host
+ * array), issued as a replayed CUDA graph.  Equivalent to calling
+ * steps_kdk_step for each dts[k], bit for bit.
+ */
+steps_status steps_kdk_run(steps_ctx *ctx, int nsteps, const double *dts);
+
+/*
+ * steps_get_state -- copy the FP64 state out in caller order.  Any pointer
+ * may be NULL to skip it.  pos/vel/acc are [n][3]; acc is the pair term at the
+ * current positions.  Synchronises the stream.
+ */
+steps_status steps_get_state(steps_ctx *ctx, double *pos, double *vel, double *acc, double *t,
+                             double *a);
+
+/*
+ * steps_set_state -- overwrite positions and velocities (caller order,
+ * [n][3], host or device) and the time/scale factor, then re-sort and
+ * recompute the pair term.  Masses and softening are kept.
+ */
+steps_status steps_set_state(steps_ctx *ctx, const double *pos, const double *vel, double t,
+                             double a);
+
+/*
+ * Exact checkpoint/resume.  steps_checkpoint_size gives the byte size of an
+ * opaque blob holding the full internal state (sorted FP64 arrays, the
+ * permutation, the stored pair term, t, a, step count).  Restoring it into a
+ * context created with the same n, masses, softening and config continues the
+ * run bit-identically to an uninterrupted one.  buf is host memory.
+ */
+steps_status steps_checkpoint_size(steps_ctx *ctx, size_t *bytes);
+steps_status steps_checkpoint_save(steps_ctx *ctx, void *buf);
+steps_status steps_checkpoint_load(steps_ctx *ctx, const void *buf);
+
+/*
+ * steps_forces_subset -- the pair term of Eq. 8 (same definition as
+ * steps_forces) for nt selected targets only, always summed in FP64 on the
+ * GPU over all n sources, at the current positions.  targets [nt] are caller
+ * indices (host or device int64); acc_out [nt][3] (host or device) receives
+ * the rows in the order given.  Used for accuracy checks and the FP64
+ * comparison timing.  EINVAL for an index outside [0, n).
+ */
+steps_status steps_forces_subset(steps_ctx *ctx, int64_t nt, const int64_t *targets, double *acc_out);
+
+/*
+ * steps_diagnostics -- FP64 diagnostics at the current state:
+ *   ekin = 1/2 sum m v^2,  p = sum m v,  epot = 1/2 sum_i sum_{j != i} G m_i m_j W(r_ij, h_i+h_j)
+ * where W is the pair potential of the spline kernel (W' = F of Eq. 4,
+ * W = -1/r for r >= h, W(0) = -2.8/h).  Any output pointer (host) may be
+ * NULL; epot costs an O(N^2) FP64 pass, so pass NULL to skip it.
+ */
+steps_status steps_diagnostics(steps_ctx *ctx, double *ekin, double *epot, double p[3]);
+
+/* Number of particles in the context. */
+int64_t steps_size(const steps_ctx *ctx);
+
+/* Release the context and all its device memory.  NULL is ignored. */
+void steps_free(steps_ctx *ctx);
+
+const char *steps_strerror(steps_status s);
+const char *steps_last_error(void);
+
+/*
+ * Testing hook: bound, in nanoseconds, for every device-side wait of the
+ * force kernels of this context (default 2e9).  A wait that runs out makes the
+ * kernel record STEPS_ETIMEOUT, drain its own copies and exit; the next
+ * synchronising call returns STEPS_ETIMEOUT.  0 makes the first wait give up.
+ */
+steps_status steps_set_wait_limit(steps_ctx *ctx, int64_t ns);
+
+/*
+ * Process-wide cap, in bytes, on the device memory this library allocates
+ * (0 = no cap, the default).  An allocation that would exceed it fails with
+ * STEPS_ENOMEM before cudaMalloc is called; used to exercise the out-of-memory
+ * path without exhausting the GPU.
+ */
+steps_status steps_set_memory_limit(size_t bytes);
+
+/*
+ * Kernel timing for benchmarks.  While enabled, the context records CUDA
+ * events around every pair-force kernel launch on its stream.
+ * steps_profile_read synchronises and returns the summed device time of those
+ * launches (ms), their count, and the number of kernels of this library the
+ * context launched since the last reset.  Any output pointer may be NULL.
+ */
+steps_status steps_profile_enable(steps_ctx *ctx, int on);
+steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force_launches,
+                                int64_t *kernel_launches, int reset);
+
+/* Force-kernel variants built into the library (for tile_override and tuning). */
+int steps_num_variants(void);
+const char *steps_variant_name(int k);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STEPS_H */

@@ -1,0 +1,818 @@
+// C ABI of libsteps: simulation contexts, force evaluation, the KDK step
+// (Eq. 9-11) and diagnostics.  Host-side runtime only; all arithmetic of the
+// method runs in the kernels of force_f32.cu, force_f64.cu, stage.cu and
+// integrate.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <vector>
+
+#include "steps_internal.h"
+
+namespace steps {
+
+static thread_local char g_last_error[512] = "";
+static size_t g_mem_limit = 0;  // process-wide cap on this library's device allocations (0: none)
+static size_t g_mem_used = 0;
+static std::mutex g_mem_mu;
+
+void set_error(const char *fmt, ...) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(g_last_error, sizeof(g_last_error), fmt, ap);
+    va_end(ap);
+}
+
+steps_status cuda_status(cudaError_t e, const char *what) {
+    set_error("%s: %s (%s)", what, cudaGetErrorName(e), cudaGetErrorString(e));
+    return e == cudaErrorMemoryAllocation ? STEPS_ENOMEM : STEPS_ECUDA;
+}
+
+}  // namespace steps
+
+using namespace steps;
+
+struct steps_ctx {
+    int64_t n = 0;
+    steps_config cfg{};
+    Cosmo cosmo{};
+    cudaStream_t st = nullptr;
+    bool own_stream = false;
+    int device = 0;
+    int num_sms = 0;
+    // FP64 master state, sorted order (SoA)
+    double *x = nullptr, *y = nullptr, *z = nullptr;
+    double *vx = nullptr, *vy = nullptr, *vz = nullptr;
+    double *m = nullptr, *h = nullptr;
+    double *ax = nullptr, *ay = nullptr, *az = nullptr;
+    int64_t *perm = nullptr;  // sorted index -> caller index
+    double *sc = nullptr;     // device scalars SC_*
+    double *red = nullptr;    // reduction scratch
+    int nred = 0;
+    double *tmp3 = nullptr;   // [n][3] caller-order staging for boundary copies
+    double *dts = nullptr;    // per-step dt for runs
+    int dts_cap = 0;
+    // FP32 staging
+    Staging stg;
+    float4 *jdup_buf = nullptr, *res_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
+    unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
+    float alpha = 0.125f;
+    int64_t np = 0, ntile_cap = 0;
+    int variant = -1;
+    ForcePlan plan;
+    double *partial = nullptr;
+    size_t partial_cap = 0;
+    SortScratch srt;
+    int *err = nullptr;       // device error word
+    int *flag = nullptr;      // device validation flags
+    long long wait_ns = 2000000000LL;
+    int64_t since_sort = 0;
+    // benchmark hooks
+    bool profiling = false;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> force_events;
+    int64_t force_launches = 0;
+    int64_t kernel_launches = 0;
+    int64_t *inv = nullptr;   // inverse permutation scratch (subset forces)
+    int64_t *tgt = nullptr;   // mapped target indices
+    int64_t tgt_cap = 0;
+    std::vector<void *> allocs;
+    std::vector<size_t> sizes;
+};
+
+namespace {
+
+steps_status dev_alloc(steps_ctx *c, void **p, size_t bytes) {
+    *p = nullptr;
+    if (bytes == 0) bytes = 16;
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        if (g_mem_limit && g_mem_used + bytes > g_mem_limit) {
+            set_error("device allocation of %zu bytes exceeds the library memory limit (%zu of %zu used)",
+                      bytes, g_mem_used, g_mem_limit);
+            return STEPS_ENOMEM;
+        }
+        g_mem_used += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        g_mem_used -= bytes;
+        return cuda_status(e, "cudaMalloc");
+    }
+    c->allocs.push_back(*p);
+    c->sizes.push_back(bytes);
+    return STEPS_OK;
+}
+
+template <typename T>
+steps_status alloc_n(steps_ctx *c, T **p, size_t count) {
+    return dev_alloc(c, reinterpret_cast<void **>(p), count * sizeof(T));
+}
+
+void dev_free(steps_ctx *c, void *p) {
+    if (!p) return;
+    for (size_t k = 0; k < c->allocs.size(); ++k) {
+        if (c->allocs[k] == p) {
+            cudaFree(p);
+            std::lock_guard<std::mutex> lk(g_mem_mu);
+            g_mem_used -= c->sizes[k];
+            c->allocs.erase(c->allocs.begin() + k);
+            c->sizes.erase(c->sizes.begin() + k);
+            return;
+        }
+    }
+}
+
+// Check the device error word and clear it.
+steps_status sync_and_check(steps_ctx *c) {
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    int e = 0;
+    STEPS_CUDA(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
+    if (e) {
+        STEPS_CUDA(cudaMemset(c->err, 0, sizeof(int)));
+        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", e);
+        return (steps_status)e;
+    }
+    return STEPS_OK;
+}
+
+int pick_variant(const steps_ctx *c) {
+    const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
+    if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())
+        return c->cfg.tile_override - 1;
+    // default: 4 targets per thread; smaller tiles for small systems
+    const int ki = c->n >= 32768 ? 4 : 2;
+    for (int k = 0; k < num_variants(); ++k) {
+        const Variant &v = variant(k);
+        if (v.comp == comp && v.KI == ki && v.W == 8) return k;
+    }
+    return 0;
+}
+
+steps_status configure_variant(steps_ctx *c, int k) {
+    const Variant &v = variant(k);
+    c->variant = k;
+    c->stg.n = c->n;
+    c->stg.np = c->np;
+    c->stg.T = 32 * v.KI;
+    c->stg.ntile = c->np / c->stg.T;
+    c->stg.jdup = c->jdup_buf;
+    c->stg.res = c->res_buf;
+    c->stg.tbox_c = c->tbc_buf;
+    c->stg.tbox_e = c->tbe_buf;
+    c->plan = plan_force(c->stg, k, c->num_sms);
+    if (c->plan.partial_elems > c->partial_cap) {
+        dev_free(c, c->partial);
+        c->partial = nullptr;
+        c->partial_cap = 0;
+        STEPS_TRY(alloc_n(c, &c->partial, c->plan.partial_elems));
+        c->partial_cap = c->plan.partial_elems;
+    }
+    return STEPS_OK;
+}
+
+// Re-sort the FP64 state into Morton order; the permutation follows.
+steps_status resort(steps_ctx *c) {
+    const int64_t n = c->n;
+    int launches = 0;
+    STEPS_CUDA(morton_sort(n, c->x, c->y, c->z, c->srt, c->st, &launches));
+    c->kernel_launches += launches + 12;
+    double **arrs[] = {&c->x, &c->y, &c->z, &c->vx, &c->vy, &c->vz, &c->m, &c->h, &c->ax, &c->ay, &c->az};
+    for (double **a : arrs) {
+        STEPS_CUDA(gather_f64(n, c->srt.vals, *a, c->srt.tmp, c->st));
+        std::swap(*a, c->srt.tmp);
+    }
+    STEPS_CUDA(gather_i64(n, c->srt.vals, c->perm, c->srt.tmpi, c->st));
+    std::swap(c->perm, c->srt.tmpi);
+    c->since_sort = 0;
+    return STEPS_OK;
+}
+
+bool capturing(const steps_ctx *c) {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(c->st, &cs);
+    return cs != cudaStreamCaptureStatusNone;
+}
+
+// Pair term at the current positions into ax, ay, az (sorted order).
+steps_status compute_forces(steps_ctx *c) {
+    const bool prof = c->profiling && !capturing(c);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (prof) {
+        STEPS_CUDA(cudaEventCreate(&e0));
+        STEPS_CUDA(cudaEventCreate(&e1));
+    }
+    if (c->cfg.prec == STEPS_F64) {
+        if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
+        STEPS_CUDA(launch_force_f64(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, 0, c->n, c->ax,
+                                    c->ay, c->az, c->st));
+        if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
+        c->kernel_launches += 1;
+    } else {
+        launch_stage(c->stg, c->x, c->y, c->z, c->m, c->h, c->st);
+        STEPS_CUDA(cudaGetLastError());
+        if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
+        STEPS_CUDA(launch_force_f32(c->plan, c->stg, c->partial, c->err, c->stats, c->alpha,
+                                    c->wait_ns, c->st));
+        if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
+        STEPS_CUDA(launch_fixup(c->plan, c->stg, c->partial, c->cosmo.G, c->ax, c->ay, c->az, c->st));
+        c->kernel_launches += 3;
+    }
+    c->force_launches += 1;
+    if (prof) c->force_events.push_back({e0, e1});
+    return STEPS_OK;
+}
+
+// One KDK step with dt already in sc[SC_DT] (Eq. 11).
+steps_status issue_step(steps_ctx *c, bool do_sort) {
+    c->kernel_launches += 4;  // kick, drift, rk4, kick
+    STEPS_CUDA(launch_kick(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->ax, c->ay, c->az, c->sc,
+                           c->cosmo, c->st));
+    STEPS_CUDA(launch_drift(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->sc, c->st));
+    STEPS_CUDA(launch_rk4(c->sc, c->cosmo, c->st));
+    if (do_sort) STEPS_TRY(resort(c));
+    STEPS_TRY(compute_forces(c));
+    STEPS_CUDA(launch_kick(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->ax, c->ay, c->az, c->sc,
+                           c->cosmo, c->st));
+    return STEPS_OK;
+}
+
+int resort_every(const steps_ctx *c) { return c->cfg.resort_every > 0 ? c->cfg.resort_every : 8; }
+
+steps_status validate(steps_ctx *c, const double *d, int64_t count, bool positive, const char *name) {
+    STEPS_CUDA(cudaMemsetAsync(c->flag, 0, sizeof(int), c->st));
+    STEPS_CUDA(launch_check_finite(count, d, positive ? 1 : 0, c->flag, c->st));
+    int f = 0;
+    STEPS_CUDA(cudaMemcpyAsync(&f, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st));
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    if (f & 1) {
+        set_error("%s contains NaN or Inf", name);
+        return STEPS_EINVAL;
+    }
+    if (f & 2) {
+        set_error("%s must be > 0", name);
+        return STEPS_EINVAL;
+    }
+    return STEPS_OK;
+}
+
+// Copy a caller [n][3] array (host or device) into sorted SoA via perm (or identity).
+steps_status load3(steps_ctx *c, const double *src, double *a, double *b, double *cc, bool via_perm) {
+    STEPS_CUDA(cudaMemcpyAsync(c->tmp3, src, sizeof(double) * 3 * c->n, cudaMemcpyDefault, c->st));
+    STEPS_TRY(validate(c, c->tmp3, 3 * c->n, false, "a position/velocity array"));
+    if (via_perm)
+        STEPS_CUDA(launch_gather3(c->n, c->perm, c->tmp3, a, b, cc, c->st));
+    else
+        STEPS_CUDA(launch_split3(c->n, c->tmp3, a, b, cc, c->st));
+    return STEPS_OK;
+}
+
+steps_status store3(steps_ctx *c, double *dst, const double *a, const double *b, const double *cc) {
+    STEPS_CUDA(launch_scatter3(c->n, c->perm, a, b, cc, c->tmp3, c->st));
+    STEPS_CUDA(cudaMemcpyAsync(dst, c->tmp3, sizeof(double) * 3 * c->n, cudaMemcpyDefault, c->st));
+    return STEPS_OK;
+}
+
+steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const double *mass,
+                       const double *soft, double h_min, double t0, double a0) {
+    const int64_t n = c->n;
+    STEPS_CUDA(cudaGetDevice(&c->device));
+    STEPS_CUDA(cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->device));
+    double **soa[] = {&c->x, &c->y, &c->z, &c->vx, &c->vy, &c->vz, &c->m, &c->h, &c->ax, &c->ay, &c->az};
+    for (double **a : soa) STEPS_TRY(alloc_n(c, a, n));
+    STEPS_TRY(alloc_n(c, &c->perm, n));
+    STEPS_TRY(alloc_n(c, &c->sc, SC_COUNT));
+    c->nred = 256;
+    STEPS_TRY(alloc_n(c, &c->red, 4 * c->nred + 8));
+    STEPS_TRY(alloc_n(c, &c->tmp3, 3 * n));
+    STEPS_TRY(alloc_n(c, &c->err, 2));
+    c->flag = c->err + 1;
+    STEPS_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->st));
+    // staging: pad to a multiple of every variant's i-block (all divide 1024)
+    c->np = (n + 1023) / 1024 * 1024;
+    c->ntile_cap = c->np / 64;
+    STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
+    STEPS_TRY(alloc_n(c, &c->res_buf, c->np));
+    STEPS_TRY(alloc_n(c, &c->stats, 2));
+    STEPS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st));
+    STEPS_TRY(alloc_n(c, &c->tbc_buf, c->ntile_cap));
+    STEPS_TRY(alloc_n(c, &c->tbe_buf, c->ntile_cap));
+    // sort scratch
+    int64_t p2 = 1;
+    while (p2 < n) p2 <<= 1;
+    c->srt.npow2 = std::max<int64_t>(p2, 2);
+    STEPS_TRY(alloc_n(c, &c->srt.keys, c->srt.npow2));
+    STEPS_TRY(alloc_n(c, &c->srt.vals, c->srt.npow2));
+    STEPS_TRY(alloc_n(c, &c->srt.bbox, 8));
+    STEPS_TRY(alloc_n(c, &c->srt.tmp, n));
+    STEPS_TRY(alloc_n(c, &c->srt.tmpi, n));
+
+    // upload (caller order == initial internal order)
+    STEPS_TRY(load3(c, pos, c->x, c->y, c->z, false));
+    if (vel) {
+        STEPS_TRY(load3(c, vel, c->vx, c->vy, c->vz, false));
+    } else {
+        STEPS_CUDA(cudaMemsetAsync(c->vx, 0, sizeof(double) * n, c->st));
+        STEPS_CUDA(cudaMemsetAsync(c->vy, 0, sizeof(double) * n, c->st));
+        STEPS_CUDA(cudaMemsetAsync(c->vz, 0, sizeof(double) * n, c->st));
+    }
+    STEPS_CUDA(cudaMemcpyAsync(c->m, mass, sizeof(double) * n, cudaMemcpyDefault, c->st));
+    STEPS_TRY(validate(c, c->m, n, true, "mass"));
+    if (soft) {
+        STEPS_CUDA(cudaMemcpyAsync(c->h, soft, sizeof(double) * n, cudaMemcpyDefault, c->st));
+    } else {
+        if (!(h_min > 0.0) || !std::isfinite(h_min)) {
+            set_error("h_min must be finite and > 0 when soft is NULL");
+            return STEPS_EINVAL;
+        }
+        STEPS_CUDA(launch_softening(n, c->m, h_min, c->h, c->red, c->st));  // Eq. 7
+    }
+    STEPS_TRY(validate(c, c->h, n, true, "softening"));
+    STEPS_CUDA(cudaMemsetAsync(c->ax, 0, sizeof(double) * n, c->st));
+    STEPS_CUDA(cudaMemsetAsync(c->ay, 0, sizeof(double) * n, c->st));
+    STEPS_CUDA(cudaMemsetAsync(c->az, 0, sizeof(double) * n, c->st));
+    STEPS_CUDA(launch_iota(n, c->perm, c->st));
+    double sc[SC_COUNT] = {0};
+    sc[SC_T] = t0;
+    sc[SC_A] = c->cosmo.comoving ? a0 : 1.0;
+    if (c->cosmo.comoving) {
+        const double ia = 1.0 / a0;
+        sc[SC_H] = c->cosmo.H0 * std::sqrt(c->cosmo.Om * ia * ia * ia + c->cosmo.Or * ia * ia * ia * ia +
+                                           c->cosmo.OL + c->cosmo.Ok * ia * ia);
+    }
+    STEPS_CUDA(cudaMemcpyAsync(c->sc, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
+    STEPS_TRY(configure_variant(c, pick_variant(c)));
+    STEPS_TRY(resort(c));
+    STEPS_TRY(compute_forces(c));
+    return sync_and_check(c);
+}
+
+}  // namespace
+
+extern "C" {
+
+steps_config steps_default_config(void) {
+    steps_config c;
+    std::memset(&c, 0, sizeof(c));
+    c.G = 1.0;
+    c.H0 = 1.0;
+    c.Om = 0.3;
+    c.OL = 0.7;
+    c.mode = STEPS_STATIC;
+    c.prec = STEPS_F32_COMP;
+    c.resort_every = 8;
+    c.tile_override = 0;
+    return c;
+}
+
+steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const double *vel,
+                        const double *mass, const double *soft, double h_min, double t0, double a0,
+                        const steps_config *cfg, void *cuda_stream) {
+    if (!out) {
+        set_error("out is NULL");
+        return STEPS_EINVAL;
+    }
+    *out = nullptr;
+    if (n <= 0 || n > (int64_t)1 << 31) {
+        set_error("n must be in [1, 2^31], got %lld", (long long)n);
+        return STEPS_EINVAL;
+    }
+    if (!pos || !mass) {
+        set_error("pos and mass are required");
+        return STEPS_EINVAL;
+    }
+    steps_config c = cfg ? *cfg : steps_default_config();
+    if (c.mode != STEPS_STATIC && c.mode != STEPS_COMOVING) {
+        set_error("unknown mode %d", c.mode);
+        return STEPS_EINVAL;
+    }
+    if (c.prec < STEPS_F32_COMP || c.prec > STEPS_F64) {
+        set_error("unknown precision %d", c.prec);
+        return STEPS_EINVAL;
+    }
+    if (c.tile_override < 0 || c.tile_override > num_variants()) {
+        set_error("tile_override %d out of range [0, %d]", c.tile_override, num_variants());
+        return STEPS_EINVAL;
+    }
+    if (c.tile_override > 0 && variant(c.tile_override - 1).comp != (c.prec == STEPS_F32_COMP) &&
+        c.prec != STEPS_F64) {
+        set_error("tile_override %d does not match the precision mode", c.tile_override);
+        return STEPS_EINVAL;
+    }
+    if (!std::isfinite(c.G) || !std::isfinite(t0) ||
+        (c.mode == STEPS_COMOVING && (!(a0 > 0.0) || !std::isfinite(a0) || !std::isfinite(c.H0)))) {
+        set_error("G, t0, H0 and a0 must be finite (a0 > 0 in comoving mode)");
+        return STEPS_EINVAL;
+    }
+    steps_ctx *ctx = new (std::nothrow) steps_ctx();
+    if (!ctx) {
+        set_error("host allocation failed");
+        return STEPS_ENOMEM;
+    }
+    ctx->n = n;
+    ctx->cfg = c;
+    ctx->cosmo = Cosmo{c.G, c.H0, c.Om, c.OL, c.Or, c.Ok, c.mode == STEPS_COMOVING ? 1 : 0};
+    if (cuda_stream) {
+        ctx->st = (cudaStream_t)cuda_stream;
+    } else {
+        cudaError_t e = cudaStreamCreateWithFlags(&ctx->st, cudaStreamNonBlocking);
+        if (e != cudaSuccess) {
+            delete ctx;
+            return cuda_status(e, "cudaStreamCreate");
+        }
+        ctx->own_stream = true;
+    }
+    steps_status s = init_impl(ctx, pos, vel, mass, soft, h_min, t0, a0);
+    if (s != STEPS_OK) {
+        steps_free(ctx);
+        return s;
+    }
+    *out = ctx;
+    return STEPS_OK;
+}
+
+steps_status steps_forces(steps_ctx *c, double *acc_out) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    STEPS_TRY(compute_forces(c));
+    if (acc_out) STEPS_TRY(store3(c, acc_out, c->ax, c->ay, c->az));
+    return sync_and_check(c);
+}
+
+steps_status steps_kdk_step(steps_ctx *c, double dt, double *a_out) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    if (!std::isfinite(dt)) {
+        set_error("dt must be finite");
+        return STEPS_EINVAL;
+    }
+    STEPS_CUDA(launch_set_scalar(c->sc, SC_DT, dt, c->st));
+    c->kernel_launches += 1;
+    const bool do_sort = ++c->since_sort >= resort_every(c);
+    STEPS_TRY(issue_step(c, do_sort));
+    if (a_out) {
+        STEPS_CUDA(cudaMemcpyAsync(a_out, c->sc + SC_A, sizeof(double), cudaMemcpyDefault, c->st));
+        return sync_and_check(c);
+    }
+    return STEPS_OK;
+}
+
+steps_status steps_kdk_run(steps_ctx *c, int nsteps, const double *dts) {
+    if (!c || nsteps < 0 || (nsteps > 0 && !dts)) {
+        set_error("bad arguments to steps_kdk_run");
+        return STEPS_EINVAL;
+    }
+    if (nsteps == 0) return STEPS_OK;
+    for (int k = 0; k < nsteps; ++k) {
+        if (!std::isfinite(dts[k])) {
+            set_error("dts[%d] is not finite", k);
+            return STEPS_EINVAL;
+        }
+    }
+    if (nsteps > c->dts_cap) {
+        dev_free(c, c->dts);
+        c->dts = nullptr;
+        c->dts_cap = 0;
+        STEPS_TRY(alloc_n(c, &c->dts, nsteps));
+        c->dts_cap = nsteps;
+    }
+    STEPS_CUDA(cudaMemcpyAsync(c->dts, dts, sizeof(double) * nsteps, cudaMemcpyDefault, c->st));
+    STEPS_CUDA(launch_set_scalar(c->sc, SC_RUN, 0.0, c->st));
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    // Capture one plain step and one step with a re-sort; replay per step.
+    // The re-sort swaps buffer pointers, so the sorting graph is re-captured
+    // (and the plain one with it) after every sort.
+    cudaGraphExec_t plain = nullptr;
+    steps_status s = STEPS_OK;
+    auto capture = [&](bool do_sort, cudaGraphExec_t *exec) -> steps_status {
+        cudaGraph_t g = nullptr;
+        STEPS_CUDA(cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal));
+        steps_status si = STEPS_OK;
+        if (launch_set_dt(c->sc, c->dts, c->st) != cudaSuccess) si = STEPS_ECUDA;
+        if (si == STEPS_OK) si = issue_step(c, do_sort);
+        cudaError_t e = cudaStreamEndCapture(c->st, &g);
+        if (si != STEPS_OK) {
+            if (g) cudaGraphDestroy(g);
+            return si;
+        }
+        if (e != cudaSuccess) return cuda_status(e, "cudaStreamEndCapture");
+        e = cudaGraphInstantiate(exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) return cuda_status(e, "cudaGraphInstantiate");
+        return STEPS_OK;
+    };
+    for (int k = 0; k < nsteps && s == STEPS_OK; ++k) {
+        const bool do_sort = ++c->since_sort >= resort_every(c);
+        if (do_sort) {
+            // a sorting step changes the buffer roles: run it directly
+            if (plain) {
+                cudaGraphExecDestroy(plain);
+                plain = nullptr;
+            }
+            if (launch_set_dt(c->sc, c->dts, c->st) != cudaSuccess) s = STEPS_ECUDA;
+            if (s == STEPS_OK) s = issue_step(c, true);
+            continue;
+        }
+        if (!plain) s = capture(false, &plain);
+        if (s == STEPS_OK) {
+            cudaError_t e = cudaGraphLaunch(plain, c->st);
+            if (e != cudaSuccess) s = cuda_status(e, "cudaGraphLaunch");
+        }
+    }
+    if (plain) cudaGraphExecDestroy(plain);
+    if (s != STEPS_OK) return s;
+    return sync_and_check(c);
+}
+
+steps_status steps_get_state(steps_ctx *c, double *pos, double *vel, double *acc, double *t,
+                             double *a) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    if (pos) {
+        STEPS_TRY(store3(c, pos, c->x, c->y, c->z));
+        STEPS_CUDA(cudaStreamSynchronize(c->st));
+    }
+    if (vel) {
+        STEPS_TRY(store3(c, vel, c->vx, c->vy, c->vz));
+        STEPS_CUDA(cudaStreamSynchronize(c->st));
+    }
+    if (acc) {
+        STEPS_TRY(store3(c, acc, c->ax, c->ay, c->az));
+        STEPS_CUDA(cudaStreamSynchronize(c->st));
+    }
+    double sc[SC_COUNT];
+    STEPS_CUDA(cudaMemcpyAsync(sc, c->sc, sizeof(sc), cudaMemcpyDeviceToHost, c->st));
+    STEPS_TRY(sync_and_check(c));
+    if (t) *t = sc[SC_T];
+    if (a) *a = sc[SC_A];
+    return STEPS_OK;
+}
+
+steps_status steps_set_state(steps_ctx *c, const double *pos, const double *vel, double t, double a) {
+    if (!c || !pos || !vel) {
+        set_error("ctx, pos and vel are required");
+        return STEPS_EINVAL;
+    }
+    if (!std::isfinite(t) || (c->cosmo.comoving && !(a > 0.0 && std::isfinite(a)))) {
+        set_error("t must be finite and a > 0");
+        return STEPS_EINVAL;
+    }
+    STEPS_TRY(load3(c, pos, c->x, c->y, c->z, true));
+    STEPS_TRY(load3(c, vel, c->vx, c->vy, c->vz, true));
+    double sc[SC_COUNT];
+    STEPS_CUDA(cudaMemcpyAsync(sc, c->sc, sizeof(sc), cudaMemcpyDeviceToHost, c->st));
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    sc[SC_T] = t;
+    if (c->cosmo.comoving) {
+        const double ia = 1.0 / a;
+        sc[SC_A] = a;
+        sc[SC_H] = c->cosmo.H0 * std::sqrt(c->cosmo.Om * ia * ia * ia + c->cosmo.Or * ia * ia * ia * ia +
+                                           c->cosmo.OL + c->cosmo.Ok * ia * ia);
+    }
+    STEPS_CUDA(cudaMemcpyAsync(c->sc, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
+    STEPS_TRY(resort(c));
+    STEPS_TRY(compute_forces(c));
+    return sync_and_check(c);
+}
+
+// Checkpoint layout: int64 header[4] = {magic, n, since_sort, variant}, then
+// double sc[SC_COUNT], 11 sorted FP64 arrays (x..az incl. m, h), int64 perm[n].
+static const int64_t kCkptMagic = 0x5354655053434b31LL;  // "STePSCK1"
+
+steps_status steps_checkpoint_size(steps_ctx *c, size_t *bytes) {
+    if (!c || !bytes) {
+        set_error("ctx and bytes are required");
+        return STEPS_EINVAL;
+    }
+    *bytes = 4 * sizeof(int64_t) + SC_COUNT * sizeof(double) + 11 * sizeof(double) * c->n +
+             sizeof(int64_t) * c->n;
+    return STEPS_OK;
+}
+
+steps_status steps_checkpoint_save(steps_ctx *c, void *buf) {
+    if (!c || !buf) {
+        set_error("ctx and buf are required");
+        return STEPS_EINVAL;
+    }
+    char *p = (char *)buf;
+    int64_t hdr[4] = {kCkptMagic, c->n, c->since_sort, c->variant};
+    std::memcpy(p, hdr, sizeof(hdr));
+    p += sizeof(hdr);
+    STEPS_CUDA(cudaMemcpyAsync(p, c->sc, SC_COUNT * sizeof(double), cudaMemcpyDefault, c->st));
+    p += SC_COUNT * sizeof(double);
+    const double *arrs[] = {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->m, c->h, c->ax, c->ay, c->az};
+    for (const double *a : arrs) {
+        STEPS_CUDA(cudaMemcpyAsync(p, a, sizeof(double) * c->n, cudaMemcpyDefault, c->st));
+        p += sizeof(double) * c->n;
+    }
+    STEPS_CUDA(cudaMemcpyAsync(p, c->perm, sizeof(int64_t) * c->n, cudaMemcpyDefault, c->st));
+    return sync_and_check(c);
+}
+
+steps_status steps_checkpoint_load(steps_ctx *c, const void *buf) {
+    if (!c || !buf) {
+        set_error("ctx and buf are required");
+        return STEPS_EINVAL;
+    }
+    const char *p = (const char *)buf;
+    int64_t hdr[4];
+    std::memcpy(hdr, p, sizeof(hdr));
+    if (hdr[0] != kCkptMagic || hdr[1] != c->n) {
+        set_error("checkpoint does not match this context (magic or n)");
+        return STEPS_EINVAL;
+    }
+    if (hdr[3] < 0 || hdr[3] >= num_variants()) {
+        set_error("checkpoint names an unknown force variant");
+        return STEPS_EINVAL;
+    }
+    p += sizeof(hdr);
+    STEPS_CUDA(cudaMemcpyAsync(c->sc, p, SC_COUNT * sizeof(double), cudaMemcpyDefault, c->st));
+    p += SC_COUNT * sizeof(double);
+    double *arrs[] = {c->x, c->y, c->z, c->vx, c->vy, c->vz, c->m, c->h, c->ax, c->ay, c->az};
+    for (double *a : arrs) {
+        STEPS_CUDA(cudaMemcpyAsync(a, p, sizeof(double) * c->n, cudaMemcpyDefault, c->st));
+        p += sizeof(double) * c->n;
+    }
+    STEPS_CUDA(cudaMemcpyAsync(c->perm, p, sizeof(int64_t) * c->n, cudaMemcpyDefault, c->st));
+    c->since_sort = hdr[2];
+    if (hdr[3] != c->variant) STEPS_TRY(configure_variant(c, (int)hdr[3]));
+    return sync_and_check(c);
+}
+
+steps_status steps_diagnostics(steps_ctx *c, double *ekin, double *epot, double p[3]) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    double *out = c->red + 4 * c->nred;  // 4 result slots after the block partials
+    double host[5] = {0, 0, 0, 0, 0};
+    if (ekin || p) {
+        STEPS_CUDA(launch_kinetic(c->n, c->vx, c->vy, c->vz, c->m, c->red, c->nred, out, c->st));
+        STEPS_CUDA(cudaMemcpyAsync(host, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
+        STEPS_CUDA(cudaStreamSynchronize(c->st));
+    }
+    if (epot) {
+        STEPS_CUDA(launch_potential_f64(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, c->tmp3,
+                                        c->st));
+        STEPS_CUDA(launch_sum(c->n, c->tmp3, c->red, c->nred, out, c->st));
+        STEPS_CUDA(cudaMemcpyAsync(&host[4], out, sizeof(double), cudaMemcpyDeviceToHost, c->st));
+    }
+    STEPS_TRY(sync_and_check(c));
+    if (ekin) *ekin = host[0];
+    if (p) {
+        p[0] = host[1];
+        p[1] = host[2];
+        p[2] = host[3];
+    }
+    if (epot) *epot = 0.5 * host[4];
+    return STEPS_OK;
+}
+
+steps_status steps_forces_subset(steps_ctx *c, int64_t nt, const int64_t *targets, double *acc_out) {
+    if (!c || nt < 0 || (nt > 0 && (!targets || !acc_out))) {
+        set_error("bad arguments to steps_forces_subset");
+        return STEPS_EINVAL;
+    }
+    if (nt == 0) return STEPS_OK;
+    if (nt > c->tgt_cap) {
+        dev_free(c, c->tgt);
+        c->tgt = nullptr;
+        c->tgt_cap = 0;
+        STEPS_TRY(alloc_n(c, &c->tgt, 2 * nt));
+        c->tgt_cap = nt;
+    }
+    if (!c->inv) STEPS_TRY(alloc_n(c, &c->inv, c->n));
+    double *out3 = nullptr;
+    STEPS_TRY(alloc_n(c, &out3, 3 * nt));
+    int64_t *caller = c->tgt + nt;
+    steps_status s = STEPS_OK;
+    int bad = 0;
+    do {
+        cudaError_t e = cudaMemsetAsync(c->flag, 0, sizeof(int), c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(caller, targets, sizeof(int64_t) * nt, cudaMemcpyDefault, c->st);
+        if (e == cudaSuccess) e = launch_map_targets(c->n, c->perm, c->inv, nt, caller, c->tgt, c->flag, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&bad, c->flag, sizeof(int), cudaMemcpyDeviceToHost, c->st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(c->st);
+        if (e != cudaSuccess) {
+            s = cuda_status(e, "steps_forces_subset (targets)");
+            break;
+        }
+        if (bad) {
+            set_error("a target index is outside [0, n)");
+            s = STEPS_EINVAL;
+            break;
+        }
+        e = launch_force_f64_list(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, nt, c->tgt, out3, c->st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(acc_out, out3, sizeof(double) * 3 * nt, cudaMemcpyDefault, c->st);
+        if (e != cudaSuccess) {
+            s = cuda_status(e, "steps_forces_subset");
+            break;
+        }
+        c->kernel_launches += 3;
+        s = sync_and_check(c);
+    } while (0);
+    cudaStreamSynchronize(c->st);
+    dev_free(c, out3);
+    return s;
+}
+
+steps_status steps_profile_enable(steps_ctx *c, int on) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    c->profiling = on != 0;
+    return STEPS_OK;
+}
+
+steps_status steps_profile_read(steps_ctx *c, double *force_ms, int64_t *force_launches,
+                                int64_t *kernel_launches, int reset) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    double ms = 0.0;
+    for (auto &ev : c->force_events) {
+        float t = 0.f;
+        STEPS_CUDA(cudaEventElapsedTime(&t, ev.first, ev.second));
+        ms += t;
+    }
+    if (force_ms) *force_ms = ms;
+    if (force_launches) *force_launches = (int64_t)c->force_events.size();
+    if (kernel_launches) *kernel_launches = c->kernel_launches;
+    if (reset) {
+        for (auto &ev : c->force_events) {
+            cudaEventDestroy(ev.first);
+            cudaEventDestroy(ev.second);
+        }
+        c->force_events.clear();
+        c->force_launches = 0;
+        c->kernel_launches = 0;
+    }
+    return STEPS_OK;
+}
+
+int64_t steps_size(const steps_ctx *c) { return c ? c->n : 0; }
+
+void steps_free(steps_ctx *c) {
+    if (!c) return;
+    cudaStreamSynchronize(c->st);
+    for (auto &ev : c->force_events) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    while (!c->allocs.empty()) dev_free(c, c->allocs.back());
+    if (c->own_stream) cudaStreamDestroy(c->st);
+    delete c;
+}
+
+const char *steps_strerror(steps_status s) {
+    switch (s) {
+        case STEPS_OK: return "ok";
+        case STEPS_EINVAL: return "invalid argument";
+        case STEPS_ENOMEM: return "out of device memory";
+        case STEPS_ECUDA: return "CUDA error";
+        case STEPS_ETIMEOUT: return "device-side wait timed out";
+        case STEPS_ENONFINITE: return "non-finite result";
+        case STEPS_EUNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+const char *steps_last_error(void) { return g_last_error; }
+
+steps_status steps_set_wait_limit(steps_ctx *c, int64_t ns) {
+    if (!c || ns < 0) {
+        set_error("ctx is NULL or ns < 0");
+        return STEPS_EINVAL;
+    }
+    c->wait_ns = ns;
+    return STEPS_OK;
+}
+
+steps_status steps_set_memory_limit(size_t bytes) {
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_limit = bytes;
+    return STEPS_OK;
+}
+
+int steps_num_variants(void) { return num_variants(); }
+
+const char *steps_variant_name(int k) {
+    if (k < 0 || k >= num_variants()) return nullptr;
+    return variant(k).name;
+}
+
+}  // extern "C"

@@ -1,0 +1,276 @@
+// Spatial sort and FP32 tile staging for the force kernels.
+//
+// The FP64 master state is kept in Morton (Z-curve) order so that every tile
+// of T consecutive particles is spatially compact.  Each step the staging
+// kernel turns the FP64 positions of a tile into FP32 offsets from that
+// tile's FP32 centre (positions "relative to tile centres"), plus the tile's
+// half-extents and largest softening, which the force kernel uses to prove a
+// whole tile pair Newtonian (r >= h_i + h_j for every pair, Eq. 4 branch 3).
+#include <cfloat>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "steps_internal.h"
+
+namespace steps {
+
+namespace {
+
+constexpr float kPadOffset = 1.0e15f;  // padding particles: far away, zero mass, zero softening
+
+template <typename T, typename Op>
+__device__ T block_reduce(T v, T *sbuf, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    const int nw = (blockDim.x + 31) >> 5;
+    T r = sbuf[0];
+    for (int w = 1; w < nw; ++w) r = op(r, sbuf[w]);
+    __syncthreads();
+    return r;
+}
+
+struct MinOp {
+    __device__ double operator()(double a, double b) const { return fmin(a, b); }
+};
+struct MaxOp {
+    __device__ double operator()(double a, double b) const { return fmax(a, b); }
+};
+struct SumOp {
+    __device__ double operator()(double a, double b) const { return a + b; }
+};
+
+// One CTA per tile, blockDim.x == T.
+__global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
+                             const double *__restrict__ y, const double *__restrict__ z,
+                             const double *__restrict__ m, const double *__restrict__ h,
+                             float4 *__restrict__ jdup, float4 *__restrict__ res,
+                             float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e) {
+    __shared__ double sbuf[32];
+    const int64_t tile = blockIdx.x;
+    const int64_t p = tile * T + threadIdx.x;
+    const bool valid = p < n;
+    double px = 0, py = 0, pz = 0, pm = 0, ph = 0;
+    if (valid) {
+        px = x[p];
+        py = y[p];
+        pz = z[p];
+        pm = m[p];
+        ph = h[p];
+    }
+    const double lox = block_reduce(valid ? px : DBL_MAX, sbuf, MinOp());
+    const double loy = block_reduce(valid ? py : DBL_MAX, sbuf, MinOp());
+    const double loz = block_reduce(valid ? pz : DBL_MAX, sbuf, MinOp());
+    const double hix = block_reduce(valid ? px : -DBL_MAX, sbuf, MaxOp());
+    const double hiy = block_reduce(valid ? py : -DBL_MAX, sbuf, MaxOp());
+    const double hiz = block_reduce(valid ? pz : -DBL_MAX, sbuf, MaxOp());
+    const double hmax = block_reduce(valid ? ph : 0.0, sbuf, MaxOp());
+    const double mass = block_reduce(valid ? pm : 0.0, sbuf, SumOp());
+    const bool any = lox <= hix;  // tile holds at least one real particle
+    // FP32 centre (exactly representable), FP64 offsets rounded once to FP32
+    const float cx = any ? __double2float_rn(0.5 * (lox + hix)) : 0.f;
+    const float cy = any ? __double2float_rn(0.5 * (loy + hiy)) : 0.f;
+    const float cz = any ? __double2float_rn(0.5 * (loz + hiz)) : 0.f;
+    const double dx = px - (double)cx, dy = py - (double)cy, dz = pz - (double)cz;
+    const double ex = block_reduce(valid ? fabs(dx) : 0.0, sbuf, MaxOp());
+    const double ey = block_reduce(valid ? fabs(dy) : 0.0, sbuf, MaxOp());
+    const double ez = block_reduce(valid ? fabs(dz) : 0.0, sbuf, MaxOp());
+    float ox, oy, oz, rx, ry, rz, fm, fh;
+    if (valid) {
+        ox = __double2float_rn(dx);
+        oy = __double2float_rn(dy);
+        oz = __double2float_rn(dz);
+        // what the FP32 offset lost: x = c + o + r to ~2^-48 relative
+        rx = __double2float_rn(dx - (double)ox);
+        ry = __double2float_rn(dy - (double)oy);
+        rz = __double2float_rn(dz - (double)oz);
+        fm = __double2float_rn(pm);
+        fh = __double2float_rn(ph);
+    } else {
+        ox = oy = oz = kPadOffset;
+        rx = ry = rz = 0.f;
+        fm = fh = 0.f;
+    }
+    jdup[2 * p] = make_float4(ox, ox, oy, oy);
+    jdup[2 * p + 1] = make_float4(oz, oz, fm, fm);
+    res[p] = make_float4(rx, ry, rz, fh);
+    if (threadIdx.x == 0) {
+        // extents and softening rounded up so the box tests stay conservative
+        tbox_c[tile] = make_float4(cx, cy, cz, __double2float_ru(hmax));
+        tbox_e[tile] = make_float4(__double2float_ru(ex), __double2float_ru(ey), __double2float_ru(ez),
+                                   __double2float_rn(mass));
+    }
+}
+
+// ---------------- Morton sort ----------------
+
+__global__ void bbox_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                            const double *__restrict__ z, double *__restrict__ bbox) {
+    // single CTA; deterministic
+    __shared__ double sbuf[32];
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        const double v[3] = {x[i], y[i], z[i]};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], v[k]);
+            hi[k] = fmax(hi[k], v[k]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double a = block_reduce(lo[k], sbuf, MinOp());
+        const double b = block_reduce(hi[k], sbuf, MaxOp());
+        if (threadIdx.x == 0) {
+            bbox[k] = a;
+            bbox[3 + k] = b;
+        }
+    }
+}
+
+__device__ __forceinline__ unsigned long long spread21(unsigned long long v) {
+    v &= 0x1fffffull;
+    v = (v | (v << 32)) & 0x1f00000000ffffull;
+    v = (v | (v << 16)) & 0x1f0000ff0000ffull;
+    v = (v | (v << 8)) & 0x100f00f00f00f00full;
+    v = (v | (v << 4)) & 0x10c30c30c30c30c3ull;
+    v = (v | (v << 2)) & 0x1249249249249249ull;
+    return v;
+}
+
+__global__ void morton_kernel(int64_t n, int64_t npow2, const double *__restrict__ x,
+                              const double *__restrict__ y, const double *__restrict__ z,
+                              const double *__restrict__ bbox, unsigned long long *__restrict__ keys,
+                              unsigned int *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npow2) return;
+    if (i >= n) {
+        keys[i] = ~0ull;
+        vals[i] = (unsigned int)i;
+        return;
+    }
+    const double span = fmax(fmax(bbox[3] - bbox[0], bbox[4] - bbox[1]), fmax(bbox[5] - bbox[2], 1e-300));
+    const double scale = 2097151.0 / span;
+    const double v[3] = {x[i], y[i], z[i]};
+    unsigned long long c[3];
+    for (int k = 0; k < 3; ++k) {
+        double q = (v[k] - bbox[k]) * scale;
+        q = fmin(fmax(q, 0.0), 2097151.0);
+        c[k] = (unsigned long long)q;
+    }
+    keys[i] = (spread21(c[0]) << 2) | (spread21(c[1]) << 1) | spread21(c[2]);
+    vals[i] = (unsigned int)i;
+}
+
+// One compare-exchange stage of a bitonic network over (key, val); ties are
+// broken by val so that the order is total and deterministic.
+__global__ void bitonic_global(int64_t npow2, int64_t j, int64_t k, unsigned long long *keys,
+                               unsigned int *vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npow2) return;
+    const int64_t l = i ^ j;
+    if (l <= i) return;
+    const bool up = (i & k) == 0;
+    const unsigned long long ki = keys[i], kl = keys[l];
+    const unsigned int vi = vals[i], vl = vals[l];
+    const bool gt = (ki > kl) || (ki == kl && vi > vl);
+    if (gt == up) {
+        keys[i] = kl;
+        keys[l] = ki;
+        vals[i] = vl;
+        vals[l] = vi;
+    }
+}
+
+// All stages with j < 1024 of one k, inside a 2048-element shared-memory block.
+__global__ void bitonic_shared(int64_t npow2, int64_t k, int64_t jstart, unsigned long long *keys,
+                               unsigned int *vals) {
+    __shared__ unsigned long long sk[2048];
+    __shared__ unsigned int sv[2048];
+    const int64_t base = (int64_t)blockIdx.x * 2048;
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+        sk[t] = keys[base + t];
+        sv[t] = vals[base + t];
+    }
+    __syncthreads();
+    for (int64_t j = jstart; j > 0; j >>= 1) {
+        for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+            const int l = t ^ (int)j;
+            if (l > t) {
+                const int64_t gi = base + t;
+                const bool up = (gi & k) == 0;
+                const unsigned long long ki = sk[t], kl = sk[l];
+                const unsigned int vi = sv[t], vl = sv[l];
+                const bool gt = (ki > kl) || (ki == kl && vi > vl);
+                if (gt == up) {
+                    sk[t] = kl;
+                    sk[l] = ki;
+                    sv[t] = vl;
+                    sv[l] = vi;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int t = threadIdx.x; t < 2048; t += blockDim.x) {
+        keys[base + t] = sk[t];
+        vals[base + t] = sv[t];
+    }
+}
+
+__global__ void gather_f64_kernel(int64_t n, const unsigned int *__restrict__ idx,
+                                  const double *__restrict__ in, double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[idx[i]];
+}
+
+__global__ void gather_i64_kernel(int64_t n, const unsigned int *__restrict__ idx,
+                                  const int64_t *__restrict__ in, int64_t *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = in[idx[i]];
+}
+
+inline unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) / tb); }
+
+}  // namespace
+
+void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
+                  const double *m, const double *h, cudaStream_t st) {
+    stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.res,
+                                                    s.tbox_c, s.tbox_e);
+}
+
+cudaError_t morton_sort(int64_t n, const double *x, const double *y, const double *z,
+                        SortScratch &s, cudaStream_t st, int *launches) {
+    const int64_t np2 = s.npow2;
+    int count = 2;
+    bbox_kernel<<<1, 1024, 0, st>>>(n, x, y, z, s.bbox);
+    morton_kernel<<<blocks_for(np2, 256), 256, 0, st>>>(n, np2, x, y, z, s.bbox, s.keys, s.vals);
+    for (int64_t k = 2; k <= np2; k <<= 1) {
+        int64_t j = k >> 1;
+        for (; j > 0; j >>= 1) {
+            if (j < 1024 && np2 >= 2048) {
+                bitonic_shared<<<(unsigned)(np2 / 2048), 1024, 0, st>>>(np2, k, j, s.keys, s.vals);
+                ++count;
+                break;
+            }
+            bitonic_global<<<blocks_for(np2, 256), 256, 0, st>>>(np2, j, k, s.keys, s.vals);
+            ++count;
+        }
+    }
+    if (launches) *launches = count;
+    return cudaGetLastError();
+}
+
+cudaError_t gather_f64(int64_t n, const unsigned int *vals, const double *in, double *out,
+                       cudaStream_t st) {
+    gather_f64_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, vals, in, out);
+    return cudaGetLastError();
+}
+
+cudaError_t gather_i64(int64_t n, const unsigned int *vals, const int64_t *in, int64_t *out,
+                       cudaStream_t st) {
+    gather_i64_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, vals, in, out);
+    return cudaGetLastError();
+}
+
+}  // namespace steps

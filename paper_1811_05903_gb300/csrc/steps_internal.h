@@ -1,0 +1,162 @@
+// Internal declarations shared by the libsteps translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/steps.h"
+
+namespace steps {
+
+// ---------------------------------------------------------------------------
+// Error handling: thread-local last-error string, status helpers.
+// ---------------------------------------------------------------------------
+void set_error(const char *fmt, ...);
+steps_status cuda_status(cudaError_t e, const char *what);
+
+#define STEPS_CUDA(call)                                                  \
+    do {                                                                  \
+        cudaError_t _e = (call);                                          \
+        if (_e != cudaSuccess) return ::steps::cuda_status(_e, #call);    \
+    } while (0)
+
+#define STEPS_TRY(expr)                         \
+    do {                                        \
+        steps_status _s = (expr);               \
+        if (_s != STEPS_OK) return _s;          \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Force-kernel variants (FP32 pair arithmetic).
+//   KI   targets per thread (even; handled as KI/2 packed pairs)
+//   W    compute warps per CTA (one extra producer warp issues the copies)
+//   NS   shared-memory stages of j tiles
+// A tile is T = 32*KI consecutive (sorted) particles sharing one FP32 centre;
+// a warp owns one tile of targets, a CTA owns W tiles (B_I = W*T targets).
+// ---------------------------------------------------------------------------
+struct Variant {
+    int KI, W, NS;
+    bool comp;
+    const char *name;
+};
+
+int num_variants();
+const Variant &variant(int k);
+
+// Device views used by the FP32 force path.
+struct Staging {
+    int64_t n = 0;        // real particles
+    int64_t np = 0;       // padded to a multiple of B_I
+    int T = 0;            // tile size (particles)
+    int64_t ntile = 0;    // np / T
+    float4 *jdup = nullptr;   // [2 np] (ox, ox, oy, oy), (oz, oz, m, m): FP32 offsets from the tile centre
+    float4 *res = nullptr;    // [np] (rx, ry, rz, h): FP32 residual x - c - o, softening
+    float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
+    float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
+};
+
+// Launch the staging kernel: FP64 sorted SoA -> FP32 tile-relative arrays.
+void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
+                  const double *m, const double *h, cudaStream_t st);
+
+// Stream-K plan for one FP32 force evaluation.
+struct ForcePlan {
+    int variant = 0;
+    int grid = 0;       // persistent CTAs
+    int smax = 0;       // max segments (i-blocks touched) per CTA
+    int64_t niblk = 0;
+    int64_t units = 0;  // niblk * ntile
+    int B_I = 0;
+    size_t partial_elems = 0;  // grid * smax * 3 * B_I doubles
+};
+
+ForcePlan plan_force(const Staging &s, int variant, int num_sms);
+size_t force_smem_bytes(int variant);
+// alpha: tile pairs whose boxes are closer than alpha * (|c_I - c_J| + |e_I| + |e_J|)
+// take the compensated near-field path.  stats (may be null) counts near/all tile pairs.
+cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial, int *err,
+                             unsigned long long *stats, float alpha, long long wait_ns,
+                             cudaStream_t st);
+cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial, double G,
+                         double *ax, double *ay, double *az, cudaStream_t st);
+
+// FP64 comparison path: direct sum over sorted FP64 SoA, targets [i0, i1).
+cudaError_t launch_force_f64(int64_t n, const double *x, const double *y, const double *z,
+                             const double *m, const double *h, double G, int64_t i0, int64_t i1,
+                             double *ax, double *ay, double *az, cudaStream_t st);
+// FP64 pair term for a list of sorted target indices; out3 is [nt][3] in list order.
+cudaError_t launch_force_f64_list(int64_t n, const double *x, const double *y, const double *z,
+                                  const double *m, const double *h, double G, int64_t nt,
+                                  const int64_t *idx, double *out3, cudaStream_t st);
+// inv[perm[k]] = k, then out[t] = inv[caller[t]]; *bad |= 1 for an index outside [0, n).
+cudaError_t launch_map_targets(int64_t n, const int64_t *perm, int64_t *inv, int64_t nt,
+                               const int64_t *caller, int64_t *out, int *bad, cudaStream_t st);
+// FP64 pair potential per particle, row[i] = sum_{j != i} G m_i m_j W(r_ij, h_i + h_j).
+cudaError_t launch_potential_f64(int64_t n, const double *x, const double *y, const double *z,
+                                 const double *m, const double *h, double G, double *row,
+                                 cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// Spatial sort (Morton order of FP64 positions).
+// ---------------------------------------------------------------------------
+struct SortScratch {
+    int64_t npow2 = 0;
+    unsigned long long *keys = nullptr;
+    unsigned int *vals = nullptr;
+    double *bbox = nullptr;   // [6] min xyz, max xyz
+    double *tmp = nullptr;    // [n] gather buffer
+    int64_t *tmpi = nullptr;  // [n]
+};
+// Sorts (key, index) pairs; *launches receives the number of kernels issued.
+cudaError_t morton_sort(int64_t n, const double *x, const double *y, const double *z,
+                        SortScratch &s, cudaStream_t st, int *launches);
+// out[k] = in[vals[k]] for k < n
+cudaError_t gather_f64(int64_t n, const unsigned int *vals, const double *in, double *out,
+                       cudaStream_t st);
+cudaError_t gather_i64(int64_t n, const unsigned int *vals, const int64_t *in, int64_t *out,
+                       cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// FP64 integrator on device.  Scalars live in device memory so that a whole
+// step can be captured in a CUDA graph.
+// ---------------------------------------------------------------------------
+enum { SC_T = 0, SC_A = 1, SC_H = 2, SC_DT = 3, SC_STEP = 4, SC_RUN = 5, SC_COUNT = 8 };
+
+struct Cosmo {
+    double G, H0, Om, OL, Or, Ok;
+    int comoving;
+};
+
+cudaError_t launch_kick(int64_t n, const double *x, const double *y, const double *z, double *vx,
+                        double *vy, double *vz, const double *ax, const double *ay,
+                        const double *az, const double *sc, const Cosmo &c, cudaStream_t st);
+cudaError_t launch_drift(int64_t n, double *x, double *y, double *z, const double *vx,
+                         const double *vy, const double *vz, const double *sc, cudaStream_t st);
+cudaError_t launch_rk4(double *sc, const Cosmo &c, cudaStream_t st);
+cudaError_t launch_set_dt(double *sc, const double *dts, cudaStream_t st);
+
+// Deterministic FP64 reductions: out[0] = sum w*v^2/2, out[1..3] = sum w*v
+cudaError_t launch_kinetic(int64_t n, const double *vx, const double *vy, const double *vz,
+                           const double *m, double *block_buf, int nblk, double *out,
+                           cudaStream_t st);
+cudaError_t launch_sum(int64_t n, const double *v, double *block_buf, int nblk, double *out,
+                       cudaStream_t st);
+
+// Scatter sorted-order FP64 SoA into caller order [n][3].
+cudaError_t launch_scatter3(int64_t n, const int64_t *perm, const double *a, const double *b,
+                            const double *c, double *out3, cudaStream_t st);
+// Gather caller order [n][3] into sorted SoA through perm (sorted k <- caller perm[k]).
+cudaError_t launch_gather3(int64_t n, const int64_t *perm, const double *in3, double *a, double *b,
+                           double *c, cudaStream_t st);
+cudaError_t launch_split3(int64_t n, const double *in3, double *a, double *b, double *c,
+                          cudaStream_t st);
+cudaError_t launch_iota(int64_t n, int64_t *perm, cudaStream_t st);
+// Eq. 7 on device: h = cbrt(m / m_min) * h_min, with m_min reduced on device.
+cudaError_t launch_softening(int64_t n, const double *m, double h_min, double *h, double *scratch,
+                             cudaStream_t st);
+// Input check: *flag |= 1 if a holds NaN/Inf, |= 2 if positive != 0 and some a[i] <= 0.
+cudaError_t launch_check_finite(int64_t n, const double *a, int positive, int *flag,
+                                cudaStream_t st);
+cudaError_t launch_set_scalar(double *sc, int slot, double v, cudaStream_t st);
+
+}  // namespace steps

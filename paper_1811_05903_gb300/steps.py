@@ -1,0 +1,280 @@
+"""Thin ctypes binding of libsteps (include/steps.h).
+
+Argument marshalling only: every step of the method runs in the CUDA library.
+The functions keep the C names.  Array arguments may be numpy arrays (host) or
+torch CUDA tensors (device); both must be C-contiguous float64.  Importing this
+module does not load the library; the first call does, and raises if the CUDA
+library is missing or cannot be loaded -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+_lib = None
+
+STEPS_OK, STEPS_EINVAL, STEPS_ENOMEM, STEPS_ECUDA, STEPS_ETIMEOUT, STEPS_ENONFINITE, STEPS_EUNSUPPORTED = range(7)
+STEPS_STATIC, STEPS_COMOVING = 0, 1
+STEPS_F32_COMP, STEPS_F32_NAIVE, STEPS_F64 = 0, 1, 2
+
+HEADER_SYMBOLS = [
+    "steps_default_config", "steps_init", "steps_forces", "steps_kdk_step", "steps_kdk_run",
+    "steps_get_state", "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
+    "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
+    "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
+    "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
+]
+
+
+class StepsError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s (status %d): %s" % (_STATUS_NAMES.get(status, "?"), status, msg))
+        self.status = status
+
+
+_STATUS_NAMES = {0: "STEPS_OK", 1: "STEPS_EINVAL", 2: "STEPS_ENOMEM", 3: "STEPS_ECUDA",
+                 4: "STEPS_ETIMEOUT", 5: "STEPS_ENONFINITE", 6: "STEPS_EUNSUPPORTED"}
+
+
+class steps_config(ctypes.Structure):
+    _fields_ = [("G", ctypes.c_double), ("H0", ctypes.c_double), ("Om", ctypes.c_double),
+                ("OL", ctypes.c_double), ("Or", ctypes.c_double), ("Ok", ctypes.c_double),
+                ("mode", ctypes.c_int), ("prec", ctypes.c_int), ("resort_every", ctypes.c_int),
+                ("tile_override", ctypes.c_int)]
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libsteps.so.  Raises OSError if it is absent (no CPU fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.LIB
+    if not os.path.exists(path):
+        if build_if_missing:
+            _build.build()
+        else:
+            raise OSError("libsteps.so is not built (%s); run __graft_entry__.build()" % path)
+    lib = ctypes.CDLL(path)
+    P, I, I64, D, S = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_size_t
+    lib.steps_default_config.restype = steps_config
+    lib.steps_init.argtypes = [ctypes.POINTER(P), I64, P, P, P, P, D, D, D, ctypes.POINTER(steps_config), P]
+    lib.steps_forces.argtypes = [P, P]
+    lib.steps_kdk_step.argtypes = [P, D, P]
+    lib.steps_kdk_run.argtypes = [P, I, P]
+    lib.steps_get_state.argtypes = [P, P, P, P, P, P]
+    lib.steps_set_state.argtypes = [P, P, P, D, D]
+    lib.steps_checkpoint_size.argtypes = [P, ctypes.POINTER(S)]
+    lib.steps_checkpoint_save.argtypes = [P, P]
+    lib.steps_checkpoint_load.argtypes = [P, P]
+    lib.steps_diagnostics.argtypes = [P, P, P, P]
+    lib.steps_size.argtypes = [P]
+    lib.steps_size.restype = I64
+    lib.steps_free.argtypes = [P]
+    lib.steps_free.restype = None
+    lib.steps_strerror.argtypes = [I]
+    lib.steps_strerror.restype = ctypes.c_char_p
+    lib.steps_last_error.restype = ctypes.c_char_p
+    lib.steps_set_wait_limit.argtypes = [P, I64]
+    lib.steps_set_memory_limit.argtypes = [S]
+    lib.steps_forces_subset.argtypes = [P, I64, P, P]
+    lib.steps_profile_enable.argtypes = [P, I]
+    lib.steps_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(I64), I]
+    lib.steps_num_variants.restype = I
+    lib.steps_variant_name.argtypes = [I]
+    lib.steps_variant_name.restype = ctypes.c_char_p
+    for name in ["steps_init", "steps_forces", "steps_kdk_step", "steps_kdk_run", "steps_get_state",
+                 "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
+                 "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
+                 "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
+                 "steps_profile_read"]:
+        getattr(lib, name).restype = I
+    _lib = lib
+    return lib
+
+
+def _check(status: int):
+    if status != STEPS_OK:
+        raise StepsError(status, _lib.steps_last_error().decode(errors="replace"))
+
+
+def ptr(a):
+    """Raw pointer of a numpy array, a torch tensor, None or an int."""
+    if a is None:
+        return None
+    if isinstance(a, int):
+        return a
+    if isinstance(a, np.ndarray):
+        if not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("arrays must be C-contiguous")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if not a.is_contiguous():
+            raise ValueError("tensors must be contiguous")
+        return a.data_ptr()
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _f64(a, shape):
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        return a.reshape(shape)
+    return a  # torch tensor: caller guarantees float64, contiguous
+
+
+def steps_default_config() -> steps_config:
+    return load().steps_default_config()
+
+
+def steps_init(pos, vel, mass, soft=None, h_min=0.0, t0=0.0, a0=1.0, cfg=None, stream=None):
+    """Returns an opaque context handle (int)."""
+    lib = load()
+    n = int(mass.shape[0])
+    pos, vel, mass, soft = _f64(pos, (n, 3)), _f64(vel, (n, 3)), _f64(mass, (n,)), _f64(soft, (n,))
+    h = ctypes.c_void_p()
+    c = cfg if cfg is not None else lib.steps_default_config()
+    _check(lib.steps_init(ctypes.byref(h), n, ptr(pos), ptr(vel), ptr(mass), ptr(soft), float(h_min),
+                          float(t0), float(a0), ctypes.byref(c), stream))
+    return h.value
+
+
+def steps_forces(ctx, acc_out=None):
+    _check(load().steps_forces(ctx, ptr(acc_out)))
+    return acc_out
+
+
+def steps_forces_subset(ctx, targets, acc_out=None):
+    """FP64-on-GPU pair term for the caller-order rows in ``targets``."""
+    if isinstance(targets, np.ndarray):
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+    nt = int(targets.shape[0])
+    if acc_out is None:
+        acc_out = np.empty((nt, 3))
+    _check(load().steps_forces_subset(ctx, nt, ptr(targets), ptr(acc_out)))
+    return acc_out
+
+
+def steps_profile_enable(ctx, on: bool = True):
+    _check(load().steps_profile_enable(ctx, 1 if on else 0))
+
+
+def steps_profile_read(ctx, reset: bool = True):
+    """(summed pair-force kernel ms, force launches, all kernel launches)."""
+    ms, fl, kl = ctypes.c_double(), ctypes.c_int64(), ctypes.c_int64()
+    _check(load().steps_profile_read(ctx, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(kl),
+                                     1 if reset else 0))
+    return ms.value, fl.value, kl.value
+
+
+def steps_kdk_step(ctx, dt: float, want_a: bool = False):
+    a = ctypes.c_double()
+    _check(load().steps_kdk_step(ctx, float(dt), ctypes.byref(a) if want_a else None))
+    return a.value if want_a else None
+
+
+def steps_kdk_run(ctx, dts):
+    dts = np.ascontiguousarray(dts, dtype=np.float64)
+    _check(load().steps_kdk_run(ctx, int(dts.size), dts.ctypes.data))
+
+
+def steps_get_state(ctx, pos=None, vel=None, acc=None):
+    t, a = ctypes.c_double(), ctypes.c_double()
+    _check(load().steps_get_state(ctx, ptr(pos), ptr(vel), ptr(acc), ctypes.byref(t), ctypes.byref(a)))
+    return t.value, a.value
+
+
+def steps_set_state(ctx, pos, vel, t: float, a: float):
+    _check(load().steps_set_state(ctx, ptr(pos), ptr(vel), float(t), float(a)))
+
+
+def steps_checkpoint_save(ctx) -> bytes:
+    lib = load()
+    size = ctypes.c_size_t()
+    _check(lib.steps_checkpoint_size(ctx, ctypes.byref(size)))
+    buf = ctypes.create_string_buffer(size.value)
+    _check(lib.steps_checkpoint_save(ctx, buf))
+    return buf.raw
+
+
+def steps_checkpoint_load(ctx, blob: bytes):
+    buf = ctypes.create_string_buffer(blob, len(blob))
+    _check(load().steps_checkpoint_load(ctx, buf))
+
+
+def steps_diagnostics(ctx, potential: bool = True):
+    ek, ep = ctypes.c_double(), ctypes.c_double()
+    p = (ctypes.c_double * 3)()
+    _check(load().steps_diagnostics(ctx, ctypes.byref(ek), ctypes.byref(ep) if potential else None, p))
+    return ek.value, (ep.value if potential else None), np.array(list(p))
+
+
+def steps_size(ctx) -> int:
+    return int(load().steps_size(ctx))
+
+
+def steps_free(ctx):
+    if ctx:
+        load().steps_free(ctx)
+
+
+def steps_set_wait_limit(ctx, ns: int):
+    _check(load().steps_set_wait_limit(ctx, int(ns)))
+
+
+def steps_set_memory_limit(nbytes: int):
+    _check(load().steps_set_memory_limit(int(nbytes)))
+
+
+def steps_variants():
+    lib = load()
+    return [lib.steps_variant_name(k).decode() for k in range(lib.steps_num_variants())]
+
+
+def make_config(mode=STEPS_STATIC, prec=STEPS_F32_COMP, G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0,
+                Ok=0.0, resort_every=8, tile_override=0) -> steps_config:
+    return steps_config(G, H0, Om, OL, Or, Ok, mode, prec, resort_every, tile_override)
+
+
+class Simulation:
+    """Convenience owner of one context (frees it on close/GC)."""
+
+    def __init__(self, pos, vel, mass, soft=None, h_min=0.0, t0=0.0, a0=1.0, cfg=None, stream=None):
+        self.n = int(mass.shape[0])
+        self.ctx = steps_init(pos, vel, mass, soft, h_min, t0, a0, cfg, stream)
+
+    def forces(self, out=None):
+        if out is None:
+            out = np.empty((self.n, 3))
+        steps_forces(self.ctx, out)
+        return out
+
+    def step(self, dt, want_a=False):
+        return steps_kdk_step(self.ctx, dt, want_a)
+
+    def run(self, dts):
+        steps_kdk_run(self.ctx, dts)
+
+    def state(self):
+        pos, vel, acc = np.empty((self.n, 3)), np.empty((self.n, 3)), np.empty((self.n, 3))
+        t, a = steps_get_state(self.ctx, pos, vel, acc)
+        return pos, vel, acc, t, a
+
+    def close(self):
+        if self.ctx:
+            steps_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
