@@ -202,6 +202,14 @@ steps_status steps_profile_enable(steps_ctx *ctx, int on);
 steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force_launches,
                                 int64_t *kernel_launches, int reset);
 
+/*
+ * Tile-pair statistics of the FP32 path since the last call (reset on read):
+ * how many target-tile x source-tile pairs were classified near field
+ * (summed with the compensated/spline path) out of all pairs visited.
+ * Synchronises the stream.
+ */
+steps_status steps_force_stats(steps_ctx *ctx, uint64_t *near_pairs, uint64_t *all_pairs);
+
 /* Force-kernel variants built into the library (for tile_override and tuning). */
 int steps_num_variants(void);
 const char *steps_variant_name(int k);

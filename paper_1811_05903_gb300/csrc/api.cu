@@ -59,9 +59,10 @@ struct steps_ctx {
     int dts_cap = 0;
     // FP32 staging
     Staging stg;
-    float4 *jdup_buf = nullptr, *res_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
+    float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
+    NearScratch nr;                       // near-field bitmap and work items
     unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
-    float alpha = 0.125f;
+    float alpha = 0.03125f;
     int64_t np = 0, ntile_cap = 0;
     int variant = -1;
     ForcePlan plan;
@@ -162,10 +163,11 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.T = 32 * v.KI;
     c->stg.ntile = c->np / c->stg.T;
     c->stg.jdup = c->jdup_buf;
-    c->stg.res = c->res_buf;
+    c->stg.rdup = c->rdup_buf;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     c->plan = plan_force(c->stg, k, c->num_sms);
+    c->nr.cap_items = 8 * c->stg.ntile;
     if (c->plan.partial_elems > c->partial_cap) {
         dev_free(c, c->partial);
         c->partial = nullptr;
@@ -217,11 +219,12 @@ steps_status compute_forces(steps_ctx *c) {
         launch_stage(c->stg, c->x, c->y, c->z, c->m, c->h, c->st);
         STEPS_CUDA(cudaGetLastError());
         if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
-        STEPS_CUDA(launch_force_f32(c->plan, c->stg, c->partial, c->err, c->stats, c->alpha,
-                                    c->wait_ns, c->st));
+        STEPS_CUDA(launch_force_f32(c->plan, c->stg, c->partial, c->nr, c->err, c->stats, c->alpha,
+                                    c->wait_ns, c->num_sms, c->st));
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
-        STEPS_CUDA(launch_fixup(c->plan, c->stg, c->partial, c->cosmo.G, c->ax, c->ay, c->az, c->st));
-        c->kernel_launches += 3;
+        STEPS_CUDA(launch_fixup(c->plan, c->stg, c->partial, c->nr, c->cosmo.G, c->ax, c->ay,
+                                c->az, c->st));
+        c->kernel_launches += 6;  // stage, far, near count, near scan, near, fixup
     }
     c->force_launches += 1;
     if (prof) c->force_events.push_back({e0, e1});
@@ -297,7 +300,14 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     c->np = (n + 1023) / 1024 * 1024;
     c->ntile_cap = c->np / 64;
     STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
-    STEPS_TRY(alloc_n(c, &c->res_buf, c->np));
+    STEPS_TRY(alloc_n(c, &c->rdup_buf, 2 * c->np));
+    STEPS_TRY(alloc_n(c, &c->nr.bits, (size_t)c->ntile_cap * ((c->ntile_cap + 31) / 32)));
+    STEPS_TRY(alloc_n(c, &c->nr.cnt, c->ntile_cap));
+    STEPS_TRY(alloc_n(c, &c->nr.item_off, c->ntile_cap + 1));
+    STEPS_TRY(alloc_n(c, &c->nr.meta, 4));
+    // near-field work-item partials: up to 8 items per target tile (the chunk
+    // size adapts on the device), 3 doubles per particle per item
+    STEPS_TRY(alloc_n(c, &c->nr.item_part, (size_t)24 * c->np));
     STEPS_TRY(alloc_n(c, &c->stats, 2));
     STEPS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st));
     STEPS_TRY(alloc_n(c, &c->tbc_buf, c->ntile_cap));
@@ -761,6 +771,20 @@ steps_status steps_profile_read(steps_ctx *c, double *force_ms, int64_t *force_l
         c->force_launches = 0;
         c->kernel_launches = 0;
     }
+    return STEPS_OK;
+}
+
+steps_status steps_force_stats(steps_ctx *c, uint64_t *near_pairs, uint64_t *all_pairs) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    unsigned long long h[2] = {0, 0};
+    STEPS_CUDA(cudaMemcpyAsync(h, c->stats, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+    STEPS_CUDA(cudaMemsetAsync(c->stats, 0, sizeof(h), c->st));
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    if (near_pairs) *near_pairs = h[0];
+    if (all_pairs) *all_pairs = h[1];
     return STEPS_OK;
 }
 

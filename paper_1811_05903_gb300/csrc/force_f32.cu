@@ -155,39 +155,83 @@ __device__ __forceinline__ void kahan2(float2 &hi, float2 &nc, const float2 p) {
     hi = t;
 }
 
+// Scalar Kahan step, same convention as kahan2 (nc holds the negated compensation).
+__device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
+    const float y = __fadd_rn(p, nc);
+    const float t = __fadd_rn(hi, y);
+    nc = __fsub_rn(y, __fsub_rn(t, hi));
+    hi = t;
+}
+
+// Tile-pair classification shared by the far-field and near-field kernels.
+// Both kernels must reach the same decision for every pair, so the test uses
+// explicitly rounded operations (no contraction into FMAs).  Conservative
+// margins of 2^-18 cover the FP32 rounding of the box arithmetic.
+//  * near if some pair may be closer than h_i + h_j (spline branches of Eq. 4);
+//  * near if the boxes are closer than alpha x (|c_I - c_J| + |e_I| + |e_J|),
+//    where one FP32 difference of offsets could lose relative precision in d.
+__device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei, const float4 cj,
+                                               const float4 ej, const float alpha2) {
+    const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
+    const float dcx = __fsub_rn(ci.x, cj.x), dcy = __fsub_rn(ci.y, cj.y), dcz = __fsub_rn(ci.z, cj.z);
+    const float gx = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcx), dn), __fmul_rn(__fadd_rn(ei.x, ej.x), up)));
+    const float gy = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcy), dn), __fmul_rn(__fadd_rn(ei.y, ej.y), up)));
+    const float gz = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcz), dn), __fmul_rn(__fadd_rn(ei.z, ej.z), up)));
+    const float gap2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
+    if (gap2 <= __fmul_rn(hs, hs)) return true;
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dcx, dcx), __fmul_rn(dcy, dcy)), __fmul_rn(dcz, dcz));
+    const float ni = __fadd_rn(__fadd_rn(__fmul_rn(ei.x, ei.x), __fmul_rn(ei.y, ei.y)), __fmul_rn(ei.z, ei.z));
+    const float nj = __fadd_rn(__fadd_rn(__fmul_rn(ej.x, ej.x), __fmul_rn(ej.y, ej.y)), __fmul_rn(ej.z, ej.z));
+    const float scale = __fadd_rn(__fadd_rn(__fsqrt_rn(n2), __fsqrt_rn(ni)), __fsqrt_rn(nj));
+    return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
+}
+
 struct ForceArgs {
     const float4 *__restrict__ jdup;   // [2 np] (ox, ox, oy, oy), (oz, oz, m, m)
-    const float4 *__restrict__ res;    // [np]   (rx, ry, rz, h): FP32 residual of the offset
+    const float4 *__restrict__ rdup;   // [2 np] (rx, rx, ry, ry), (rz, rz, h, h): offset residual, softening
     const float4 *__restrict__ tbox_c; // [ntile] (cx, cy, cz, hmax)
     const float4 *__restrict__ tbox_e; // [ntile] (ex, ey, ez, tile mass)
-    double *__restrict__ partial;
+    double *__restrict__ partial;      // far field: per-CTA, per-segment partial sums
+    double *__restrict__ item_part;    // near field: [items][3][T] partial sums
+    uint32_t *__restrict__ nearbits;   // [ntile][words]: tile pair (I, J) is near
+    const int *__restrict__ near_cnt;  // [ntile] near tiles per target tile
+    const int64_t *__restrict__ item_off;  // [ntile + 1] first work item of each target tile
+    int64_t *near_meta;                // {chunk, items, work counter}
     int *err;
     unsigned long long *stats;         // [2]: near tile pairs, all tile pairs (may be null)
     int64_t ntile;
+    int64_t words;                     // 32-bit words per bitmap row
     int64_t units;
     int smax;
-    float alpha2;                      // near-field criterion (gap < alpha * scale), squared
+    float alpha2;                      // near-field criterion, squared
     long long wait_ns;
 };
 
-// Pair term over all tile pairs of this CTA's stream-K range.
+// Far field of the pair term over this CTA's stream-K range of tile pairs.
 //   KI    targets per thread (KI/2 packed pairs), T = 32 KI particles per tile
 //   W     compute warps; warp w owns target tile (block * W + w)
 //   NS    shared-memory stages of j tiles
 //   COMP  compensated (Kahan, every FOLD j) or naive FP32 running sums
+// The producer warp streams j tiles with TMA bulk copies and, per tile and
+// compute warp, classifies the tile pair, records near pairs in the bitmap
+// (summed later by near_f32_kernel) and stages c_I - c_J (split exactly into
+// a float and its rounding error) and the tile mass in shared memory.  The
+// compute warps then only see far tile pairs, all of equal cost.
 template <int KI, int W, int NS, bool COMP, int FOLD, int MINB>
 __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
     constexpr int NPAIR = KI / 2;
     constexpr int B_I = W * T;
     constexpr uint32_t BYTES_J = T * 32u;
-    constexpr uint32_t BYTES_R = T * 16u;
     static_assert(T % FOLD == 0, "fold length must divide the tile");
+    static_assert(W <= 32, "one producer lane per compute warp");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *sj = reinterpret_cast<float4 *>(smem);
-    float4 *sr = reinterpret_cast<float4 *>(smem + NS * BYTES_J);
-    uint64_t *bars = reinterpret_cast<uint64_t *>(smem + NS * (BYTES_J + BYTES_R));
+    float4 *sj = reinterpret_cast<float4 *>(smem);                                // [NS][2T]
+    float4 *smeta = reinterpret_cast<float4 *>(smem + NS * BYTES_J);              // [NS][W][2]
+    float4 *sipos = smeta + NS * W * 2;                                           // [W][T]
+    uint64_t *bars = reinterpret_cast<uint64_t *>(sipos + W * T);                 // full[NS], empty[NS]
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -207,58 +251,96 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
     __syncthreads();
 
     if (warp == W) {
-        // ---------------- producer warp: stream j tiles ----------------
-        if (lane == 0) {
-            int64_t k = 0;
-            bool ok = true;
-            for (; k < count; ++k) {
-                const int s = (int)(k % NS);
-                if (k >= NS &&
-                    !mbar_wait_bounded(smem_u32(&bars[NS + s]), (uint32_t)(((k / NS) - 1) & 1),
-                                       a.wait_ns)) {
+        // ---------------- producer warp ----------------
+        int64_t k = 0;
+        bool ok = true;
+        int64_t cur_blk = -1;
+        float4 ci = make_float4(0.f, 0.f, 0.f, 0.f), ei = ci;
+        unsigned long long n_near = 0;
+        for (; k < count; ++k) {
+            const int s = (int)(k % NS);
+            const int64_t u = u0 + k;
+            const int64_t blk = u / a.ntile;
+            const int64_t jt = u - blk * a.ntile;
+            if (blk != cur_blk) {
+                cur_blk = blk;
+                if (lane < W) {
+                    ci = a.tbox_c[blk * W + lane];
+                    ei = a.tbox_e[blk * W + lane];
+                }
+            }
+            const float4 cj = a.tbox_c[jt];
+            const float4 ej = a.tbox_e[jt];
+            bool near = false;
+            float dcx = 0.f, dcy = 0.f, dcz = 0.f, edx = 0.f, edy = 0.f, edz = 0.f;
+            if (lane < W) {
+                near = tile_pair_near(ci, ei, cj, ej, a.alpha2);
+                dcx = two_diff(ci.x, cj.x, edx);
+                dcy = two_diff(ci.y, cj.y, edy);
+                dcz = two_diff(ci.z, cj.z, edz);
+                if (near) {
+                    const int64_t itile = blk * W + lane;
+                    atomicOr(&a.nearbits[itile * a.words + (jt >> 5)], 1u << (jt & 31));
+                    ++n_near;
+                }
+            }
+            if (k >= NS) {
+                bool got = true;
+                if (lane == 0)
+                    got = mbar_wait_bounded(smem_u32(&bars[NS + s]), (uint32_t)(((k / NS) - 1) & 1),
+                                            a.wait_ns);
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
                     ok = false;
                     break;
                 }
-                const int64_t jt = (u0 + k) % a.ntile;
-                const uint32_t full = smem_u32(&bars[s]);
-                mbar_arrive_expect_tx(full, BYTES_J + BYTES_R);
-                bulk_g2s(smem_u32(sj + (size_t)s * 2 * T), a.jdup + jt * 2 * T, BYTES_J, full);
-                bulk_g2s(smem_u32(sr + (size_t)s * T), a.res + jt * T, BYTES_R, full);
             }
+            if (lane < W) {
+                smeta[(s * W + lane) * 2] = make_float4(dcx, dcy, dcz, ej.w);
+                smeta[(s * W + lane) * 2 + 1] = make_float4(edx, edy, edz, near ? 1.f : 0.f);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();  // the other lanes' metadata before the release-arrive
+                const uint32_t full = smem_u32(&bars[s]);
+                mbar_arrive_expect_tx(full, BYTES_J);
+                bulk_g2s(smem_u32(sj + (size_t)s * 2 * T), a.jdup + jt * 2 * T, BYTES_J, full);
+            }
+        }
+        if (lane == 0) {
             if (!ok) atomicExch(a.err, (int)STEPS_ETIMEOUT);
-            // drain: every copy this thread issued must land before the CTA may exit
+            // drain: every copy this warp issued must land before the CTA may exit
             const int64_t first = k > NS ? k - NS : 0;
             for (int64_t q = first; q < k; ++q)
                 if (!mbar_wait_bounded(smem_u32(&bars[q % NS]), (uint32_t)((q / NS) & 1), kDrainNs))
                     atomicExch(a.err, (int)STEPS_ETIMEOUT);
+        }
+        if (a.stats) {
+            for (int o = 16; o > 0; o >>= 1) n_near += __shfl_xor_sync(0xffffffffu, n_near, o);
+            if (lane == 0) {
+                atomicAdd(&a.stats[0], n_near);
+                atomicAdd(&a.stats[1], (unsigned long long)(count * W));
+            }
         }
         return;
     }
 
     // ---------------- compute warps ----------------
     const float2 neg1 = make_float2(-1.0f, -1.0f);
-    unsigned long long n_near = 0, n_all = 0;
+    float4 *myipos = sipos + warp * T;
     int64_t u = u0;
     int64_t k = 0;
     int seg = 0;
     while (u < u1) {
         const int64_t blk = u / a.ntile;
         const int64_t seg_end = min(u1, (blk + 1) * a.ntile);
-        const int64_t itile = blk * W + warp;
-        const float4 ci = a.tbox_c[itile];
-        const float4 ei = a.tbox_e[itile];
-        const int64_t ibase = itile * T + lane * KI;
-
-        float2 xi[NPAIR], yi[NPAIR], zi[NPAIR];
+        const int64_t ibase = (blk * W + warp) * T + lane * KI;
+        // stash this lane's target offsets in shared memory (read again per tile)
+        __syncwarp();
 #pragma unroll
-        for (int q = 0; q < NPAIR; ++q) {
-            const float4 p0 = a.jdup[2 * (ibase + 2 * q)];
-            const float4 p0z = a.jdup[2 * (ibase + 2 * q) + 1];
-            const float4 p1 = a.jdup[2 * (ibase + 2 * q + 1)];
-            const float4 p1z = a.jdup[2 * (ibase + 2 * q + 1) + 1];
-            xi[q] = make_float2(p0.x, p1.x);
-            yi[q] = make_float2(p0.z, p1.z);
-            zi[q] = make_float2(p0z.x, p1z.x);
+        for (int t = 0; t < KI; ++t) {
+            const float4 p = a.jdup[2 * (ibase + t)];
+            const float4 pz = a.jdup[2 * (ibase + t) + 1];
+            myipos[lane * KI + t] = make_float4(p.x, p.z, pz.x, 0.f);
         }
         float2 hx[NPAIR], hy[NPAIR], hz[NPAIR];     // running sums
         float2 cx_[NPAIR], cy_[NPAIR], cz_[NPAIR];  // Kahan terms (negated), COMP only
@@ -274,64 +356,37 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                 if (lane == 0) atomicExch(a.err, (int)STEPS_ETIMEOUT);
                 return;
             }
-            const int64_t jt = u - blk * a.ntile;
-            const float4 cj = a.tbox_c[jt];
-            const float4 ej = a.tbox_e[jt];
-            const float dcx = ci.x - cj.x, dcy = ci.y - cj.y, dcz = ci.z - cj.z;
-            // Warp-uniform classification of the tile pair (conservative margins of
-            // 2^-18 cover the FP32 rounding here):
-            //  * near if any pair may be closer than h_i + h_j (spline of Eq. 4), or
-            //  * near if the boxes are closer than alpha times the offset scale, where
-            //    FP32 offsets alone could lose relative precision in d.
-            const float gx = fmaxf(0.f, fabsf(dcx) * (1.0f - 0x1p-18f) - (ei.x + ej.x) * (1.0f + 0x1p-18f));
-            const float gy = fmaxf(0.f, fabsf(dcy) * (1.0f - 0x1p-18f) - (ei.y + ej.y) * (1.0f + 0x1p-18f));
-            const float gz = fmaxf(0.f, fabsf(dcz) * (1.0f - 0x1p-18f) - (ei.z + ej.z) * (1.0f + 0x1p-18f));
-            const float gap2 = gx * gx + gy * gy + gz * gz;
-            const float hs = (ci.w + cj.w) * (1.0f + 0x1p-18f);
-            const float scale = sqrtf(dcx * dcx + dcy * dcy + dcz * dcz) +
-                                sqrtf(ei.x * ei.x + ei.y * ei.y + ei.z * ei.z) +
-                                sqrtf(ej.x * ej.x + ej.y * ej.y + ej.z * ej.z);
-            const bool near = gap2 <= hs * hs || gap2 < a.alpha2 * scale * scale;
-            n_near += near;
-            n_all += 1;
-
-            // negated target positions in the j tile's frame: -(o_i + (c_I - c_J))
-            float2 nx[NPAIR], ny[NPAIR], nz[NPAIR];
-            {
-                const float2 ndx = make_float2(-dcx, -dcx), ndy = make_float2(-dcy, -dcy),
-                             ndz = make_float2(-dcz, -dcz);
-#pragma unroll
-                for (int q = 0; q < NPAIR; ++q) {
-                    nx[q] = __ffma2_rn(xi[q], neg1, ndx);
-                    ny[q] = __ffma2_rn(yi[q], neg1, ndy);
-                    nz[q] = __ffma2_rn(zi[q], neg1, ndz);
-                }
-            }
-            const float4 *S = sj + (size_t)s * 2 * T;
-            const float4 *R = sr + (size_t)s * T;
-            if (!near) {
-                // Far field.  xs = fl(o_i + dc) loses xs_lo = (o_i + c_I - c_J) - xs, and
-                // that loss is the same for every j of the tile: left alone it would act
-                // as a coherent shift of the target.  Undo it to first order with the
-                // tile's monopole tidal tensor: p -= M (xs_lo/R^3 - 3 D (D.xs_lo)/R^5),
+            const float4 m0 = smeta[(s * W + warp) * 2];
+            const float4 m1 = smeta[(s * W + warp) * 2 + 1];
+            if (m1.w == 0.f) {
+                // Far tile pair.  xs = fl(o_i + dc) loses xs_lo = (o_i + c_I - c_J) - xs,
+                // and that loss is the same for every j of the tile: left alone it would
+                // act as a coherent shift of the target.  Undo it to first order with
+                // the tile's monopole tidal tensor, p -= M (xs_lo/R^3 - 3 D (D.xs_lo)/R^5),
                 // D = c_J - x_i ~ -xs.  Fast2Sum (|dc| >= |o_i| off the near field)
-                // gives the rounding error of xs; two_diff that of dc.
-                float2 ccx[NPAIR], ccy[NPAIR], ccz[NPAIR];
+                // gives the rounding error of xs; the producer split dc exactly.
+                float2 nx[NPAIR], ny[NPAIR], nz[NPAIR];
+                float2 px[NPAIR], py[NPAIR], pz[NPAIR];
                 {
-                    float edx, edy, edz;
-                    two_diff(ci.x, cj.x, edx);
-                    two_diff(ci.y, cj.y, edy);
-                    two_diff(ci.z, cj.z, edz);
-                    const float2 dcx2 = make_float2(dcx, dcx), dcy2 = make_float2(dcy, dcy),
-                                 dcz2 = make_float2(dcz, dcz);
-                    const float2 edx2 = make_float2(edx, edx), edy2 = make_float2(edy, edy),
-                                 edz2 = make_float2(edz, edz);
-                    const float2 M2 = make_float2(ej.w, ej.w);
+                    const float2 dcx2 = make_float2(m0.x, m0.x), dcy2 = make_float2(m0.y, m0.y),
+                                 dcz2 = make_float2(m0.z, m0.z);
+                    const float2 edx2 = make_float2(m1.x, m1.x), edy2 = make_float2(m1.y, m1.y),
+                                 edz2 = make_float2(m1.z, m1.z);
+                    const float2 ndx = make_float2(-m0.x, -m0.x), ndy = make_float2(-m0.y, -m0.y),
+                                 ndz = make_float2(-m0.z, -m0.z);
+                    const float2 M2 = make_float2(m0.w, m0.w);
 #pragma unroll
                     for (int q = 0; q < NPAIR; ++q) {
-                        const float2 lx = __fadd2_rn(__fadd2_rn(xi[q], __fadd2_rn(nx[q], dcx2)), edx2);
-                        const float2 ly = __fadd2_rn(__fadd2_rn(yi[q], __fadd2_rn(ny[q], dcy2)), edy2);
-                        const float2 lz = __fadd2_rn(__fadd2_rn(zi[q], __fadd2_rn(nz[q], dcz2)), edz2);
+                        const float4 i0 = myipos[lane * KI + 2 * q];
+                        const float4 i1 = myipos[lane * KI + 2 * q + 1];
+                        const float2 xi = make_float2(i0.x, i1.x), yi = make_float2(i0.y, i1.y),
+                                     zi = make_float2(i0.z, i1.z);
+                        nx[q] = __ffma2_rn(xi, neg1, ndx);
+                        ny[q] = __ffma2_rn(yi, neg1, ndy);
+                        nz[q] = __ffma2_rn(zi, neg1, ndz);
+                        const float2 lx = __fadd2_rn(__fadd2_rn(xi, __fadd2_rn(nx[q], dcx2)), edx2);
+                        const float2 ly = __fadd2_rn(__fadd2_rn(yi, __fadd2_rn(ny[q], dcy2)), edy2);
+                        const float2 lz = __fadd2_rn(__fadd2_rn(zi, __fadd2_rn(nz[q], dcz2)), edz2);
                         float2 R2 = __fmul2_rn(nx[q], nx[q]);
                         R2 = __ffma2_rn(ny[q], ny[q], R2);
                         R2 = __ffma2_rn(nz[q], nz[q], R2);
@@ -341,32 +396,26 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                         float2 proj = __fmul2_rn(nx[q], lx);
                         proj = __ffma2_rn(ny[q], ly, proj);
                         proj = __ffma2_rn(nz[q], lz, proj);
-                        const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
+                        const float2 k2 =
+                            __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
                         const float2 nk1 = __fmul2_rn(k1, neg1);
-                        ccx[q] = __ffma2_rn(k2, nx[q], __fmul2_rn(nk1, lx));
-                        ccy[q] = __ffma2_rn(k2, ny[q], __fmul2_rn(nk1, ly));
-                        ccz[q] = __ffma2_rn(k2, nz[q], __fmul2_rn(nk1, lz));
-                    }
-                }
-#pragma unroll 1
-                for (int j0 = 0; j0 < T; j0 += FOLD) {
-                    float2 px[NPAIR], py[NPAIR], pz[NPAIR];
-#pragma unroll
-                    for (int q = 0; q < NPAIR; ++q) {
+                        const float2 cxq = __ffma2_rn(k2, nx[q], __fmul2_rn(nk1, lx));
+                        const float2 cyq = __ffma2_rn(k2, ny[q], __fmul2_rn(nk1, ly));
+                        const float2 czq = __ffma2_rn(k2, nz[q], __fmul2_rn(nk1, lz));
                         if (COMP) {
-                            if (j0 == 0) {
-                                px[q] = ccx[q];
-                                py[q] = ccy[q];
-                                pz[q] = ccz[q];
-                            } else {
-                                px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
-                            }
+                            px[q] = cxq;
+                            py[q] = cyq;
+                            pz[q] = czq;
                         } else {
-                            px[q] = hx[q];
-                            py[q] = hy[q];
-                            pz[q] = hz[q];
+                            px[q] = __fadd2_rn(hx[q], cxq);
+                            py[q] = __fadd2_rn(hy[q], cyq);
+                            pz[q] = __fadd2_rn(hz[q], czq);
                         }
                     }
+                }
+                const float4 *S = sj + (size_t)s * 2 * T;
+#pragma unroll 1
+                for (int j0 = 0; j0 < T; j0 += FOLD) {
 #pragma unroll 2
                     for (int j = j0; j < j0 + FOLD; ++j) {
                         const float4 A = S[2 * j];
@@ -392,91 +441,22 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                             pz[q] = __ffma2_rn(sc, dz, pz[q]);
                         }
                     }
+                    if (COMP) {
 #pragma unroll
-                    for (int q = 0; q < NPAIR; ++q) {
-                        if (COMP) {
+                        for (int q = 0; q < NPAIR; ++q) {
                             kahan2(hx[q], cx_[q], px[q]);
                             kahan2(hy[q], cy_[q], py[q]);
                             kahan2(hz[q], cz_[q], pz[q]);
-                        } else {
-                            hx[q] = px[q];
-                            hy[q] = py[q];
-                            hz[q] = pz[q];
+                            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
                         }
                     }
                 }
-            } else {
-                // Near field: separation with the FP32 residuals of both offsets and the
-                // exact rounding errors of c_I - c_J and o_i + (c_I - c_J), i.e. d to
-                // ~1 ulp of |d| however large the tiles are; full spline kernel.
-                float edx, edy, edz;
-                two_diff(ci.x, cj.x, edx);
-                two_diff(ci.y, cj.y, edy);
-                two_diff(ci.z, cj.z, edz);
+                if (!COMP) {
 #pragma unroll
-                for (int q = 0; q < NPAIR; ++q) {
-                    // per target of this pair: -(r_i + err(c_I - c_J) + err(o_i + dc)), h_i
-                    float nrx[2], nry[2], nrz[2], hI[2];
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float4 ri4 = a.res[ibase + 2 * q + e];
-                        float esx, esy, esz;
-                        two_sum(e ? xi[q].y : xi[q].x, dcx, esx);
-                        two_sum(e ? yi[q].y : yi[q].x, dcy, esy);
-                        two_sum(e ? zi[q].y : zi[q].x, dcz, esz);
-                        nrx[e] = -((ri4.x + edx) + esx);
-                        nry[e] = -((ri4.y + edy) + esy);
-                        nrz[e] = -((ri4.z + edz) + esz);
-                        hI[e] = ri4.w;
-                    }
-#pragma unroll 1
-                    for (int j0 = 0; j0 < T; j0 += FOLD) {
-                        float2 px, py, pz;
-                        if (COMP) {
-                            px = py = pz = make_float2(0.f, 0.f);
-                        } else {
-                            px = hx[q];
-                            py = hy[q];
-                            pz = hz[q];
-                        }
-#pragma unroll 1
-                        for (int j = j0; j < j0 + FOLD; ++j) {
-                            const float4 A = S[2 * j];
-                            const float4 B = S[2 * j + 1];
-                            const float4 Rj = R[j];
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float dx = (A.x + (e ? nx[q].y : nx[q].x)) + (Rj.x + nrx[e]);
-                                const float dy = (A.z + (e ? ny[q].y : ny[q].x)) + (Rj.y + nry[e]);
-                                const float dz = (B.x + (e ? nz[q].y : nz[q].x)) + (Rj.z + nrz[e]);
-                                const float r2 = fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-                                if (r2 > 0.f) {  // r2 == 0: the particle itself or a coincident one
-                                    const float H = hI[e] + Rj.w;
-                                    const float ri = rsqrt_approx(r2);
-                                    const float g =
-                                        (r2 >= H * H) ? ri * ri * ri : spline_over_r_f32(r2 * ri, H);
-                                    const float sc = B.z * g;
-                                    if (e) {
-                                        px.y = fmaf(sc, dx, px.y);
-                                        py.y = fmaf(sc, dy, py.y);
-                                        pz.y = fmaf(sc, dz, pz.y);
-                                    } else {
-                                        px.x = fmaf(sc, dx, px.x);
-                                        py.x = fmaf(sc, dy, py.x);
-                                        pz.x = fmaf(sc, dz, pz.x);
-                                    }
-                                }
-                            }
-                        }
-                        if (COMP) {
-                            kahan2(hx[q], cx_[q], px);
-                            kahan2(hy[q], cy_[q], py);
-                            kahan2(hz[q], cz_[q], pz);
-                        } else {
-                            hx[q] = px;
-                            hy[q] = py;
-                            hz[q] = pz;
-                        }
+                    for (int q = 0; q < NPAIR; ++q) {
+                        hx[q] = px[q];
+                        hy[q] = py[q];
+                        hz[q] = pz[q];
                     }
                 }
             }
@@ -498,9 +478,323 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
         }
         ++seg;
     }
-    if (a.stats && lane == 0) {
-        atomicAdd(&a.stats[0], n_near);
-        atomicAdd(&a.stats[1], n_all);
+}
+
+// Index of the first set bit >= pos in a bitmap row of `words` words, or -1.
+// Warp-cooperative (32 words per probe); every lane returns the same value.
+__device__ __forceinline__ int64_t next_near(const uint32_t *__restrict__ row, int64_t words,
+                                             int64_t pos, int lane) {
+    for (int64_t w0 = pos >> 5; w0 < words; w0 += 32) {
+        const int64_t wi = w0 + lane;
+        uint32_t v = (wi < words) ? row[wi] : 0u;
+        if (wi == (pos >> 5)) v &= ~0u << (pos & 31);
+        const unsigned any = __ballot_sync(0xffffffffu, v != 0u);
+        if (any) {
+            const int l = __ffs(any) - 1;
+            const uint32_t vv = __shfl_sync(0xffffffffu, v, l);
+            return (w0 + l) * 32 + (__ffs(vv) - 1);
+        }
+    }
+    return -1;
+}
+
+constexpr int kNearWarps = 4;   // warps per CTA of the near-field kernel
+constexpr int kNearChunk = 32;  // near tiles per work item (raised on device if needed)
+
+// Rank-th set bit (0-based) of a bitmap row, or -1; warp-cooperative.
+__device__ __forceinline__ int64_t select_near(const uint32_t *__restrict__ row, int64_t words,
+                                               int64_t rank, int lane) {
+    int64_t seen = 0;
+    for (int64_t w0 = 0; w0 < words; w0 += 32) {
+        const int64_t wi = w0 + lane;
+        const uint32_t v = (wi < words) ? row[wi] : 0u;
+        int c = __popc(v), incl = c;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        const int total = __shfl_sync(0xffffffffu, incl, 31);
+        if (seen + total > rank) {
+            const unsigned hit = __ballot_sync(0xffffffffu, seen + incl > rank);
+            const int l = __ffs(hit) - 1;
+            uint32_t vv = __shfl_sync(0xffffffffu, v, l);
+            int r = (int)(rank - seen - (__shfl_sync(0xffffffffu, incl, l) - __popc(vv)));
+            for (; r > 0; --r) vv &= vv - 1;
+            return (w0 + l) * 32 + (__ffs(vv) - 1);
+        }
+        seen += total;
+    }
+    return -1;
+}
+
+// Per target tile: number of near source tiles (one warp per row).
+__global__ void near_count_kernel(const uint32_t *__restrict__ bits, int64_t ntile, int64_t words,
+                                  int *__restrict__ cnt) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= ntile) return;
+    int c = 0;
+    for (int64_t w = lane; w < words; w += 32) c += __popc(bits[row * words + w]);
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if (lane == 0) cnt[row] = c;
+}
+
+// Work items: row r contributes ceil(cnt[r] / chunk) items; item_off is the
+// exclusive scan.  chunk starts at kNearChunk and grows if the item buffer
+// (cap items) would overflow.  meta = {chunk, items, work counter}.  One CTA.
+__global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int64_t cap,
+                                 int64_t *__restrict__ item_off, int64_t *__restrict__ meta) {
+    __shared__ int64_t part[1024];
+    __shared__ int64_t s_chunk;
+    const int t = threadIdx.x;
+    const int64_t per = (ntile + blockDim.x - 1) / blockDim.x;
+    const int64_t r0 = t * per, r1 = min(ntile, r0 + per);
+    int64_t tot = 0;
+    for (int64_t r = r0; r < r1; ++r) tot += cnt[r];
+    part[t] = tot;
+    __syncthreads();
+    if (t == 0) {
+        int64_t all = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) all += part[k];
+        int64_t chunk = kNearChunk;
+        while (ntile + (all + chunk - 1) / chunk > cap) chunk *= 2;
+        s_chunk = chunk;
+    }
+    __syncthreads();
+    const int64_t chunk = s_chunk;
+    int64_t items = 0;
+    for (int64_t r = r0; r < r1; ++r) items += (cnt[r] + chunk - 1) / chunk;
+    __syncthreads();
+    part[t] = items;
+    __syncthreads();
+    if (t == 0) {
+        int64_t run = 0;
+        for (int k = 0; k < (int)blockDim.x; ++k) {
+            const int64_t v = part[k];
+            part[k] = run;
+            run += v;
+        }
+        meta[0] = chunk;
+        meta[1] = run;
+        meta[2] = 0;
+        item_off[ntile] = run;
+    }
+    __syncthreads();
+    int64_t run = part[t];
+    for (int64_t r = r0; r < r1; ++r) {
+        item_off[r] = run;
+        run += (cnt[r] + chunk - 1) / chunk;
+    }
+}
+
+// Near field of the pair term.  Work items are chunks of the near tiles of one
+// target tile (row of the bitmap); persistent warps claim items from a
+// counter, so rows with many near tiles spread over many warps.  Each item
+// writes its own partial sums (item_part[item][c][T]), which the fixup adds
+// in item order: deterministic.  Within an item the j tiles are
+// double-buffered with TMA bulk copies.  The separation carries the FP32
+// residuals of both offsets and the exact rounding errors of c_I - c_J and
+// o_i + (c_I - c_J): d to ~1 ulp of |d| however large the tiles are.  Pairs
+// are summed in packed FP32x2 on the Newtonian branch; where some lane of the
+// warp meets a pair inside h_i + h_j the full spline of Eq. 4 is taken for
+// that source.  Self pairs (d == 0 exactly) contribute nothing.
+template <int KI, bool COMP, int FOLD>
+__global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceArgs a) {
+    constexpr int T = 32 * KI;
+    constexpr int NPAIR = KI / 2;
+    constexpr uint32_t BYTES = T * 64u;  // jdup + rdup of one tile
+    extern __shared__ __align__(128) unsigned char smem[];
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    float4 *buf = reinterpret_cast<float4 *>(smem) + (size_t)warp * 2 * 4 * T;  // [2][jdup 2T | rdup 2T]
+    uint64_t *bars =
+        reinterpret_cast<uint64_t *>(reinterpret_cast<float4 *>(smem) + kNearWarps * 8 * T) + 2 * warp;
+    if (lane == 0) {
+        mbar_init(smem_u32(&bars[0]), 1);
+        mbar_init(smem_u32(&bars[1]), 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    const int64_t chunk = a.near_meta[0];
+    const int64_t items = a.near_meta[1];
+    unsigned long long *counter = reinterpret_cast<unsigned long long *>(&a.near_meta[2]);
+    int64_t uses[2] = {0, 0};  // completed uses of each buffer (phase parity)
+    auto issue = [&](int64_t jt, int b) {
+        if (lane == 0) {
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t bar = smem_u32(&bars[b]);
+            float4 *dst = buf + (size_t)b * 4 * T;
+            mbar_arrive_expect_tx(bar, BYTES);
+            bulk_g2s(smem_u32(dst), a.jdup + jt * 2 * T, T * 32u, bar);
+            bulk_g2s(smem_u32(dst + 2 * T), a.rdup + jt * 2 * T, T * 32u, bar);
+        }
+    };
+    for (;;) {
+        int64_t item = 0;
+        if (lane == 0) item = (int64_t)atomicAdd(counter, 1ull);
+        item = __shfl_sync(0xffffffffu, item, 0);
+        if (item >= items) break;
+        // row = last r with item_off[r] <= item
+        int64_t lo = 0, hi_r = a.ntile;  // item_off[lo] <= item < item_off[hi_r]
+        while (hi_r - lo > 1) {
+            const int64_t mid = (lo + hi_r) >> 1;
+            if (a.item_off[mid] <= item) lo = mid; else hi_r = mid;
+        }
+        const int64_t itile = lo;
+        const int64_t first = (item - a.item_off[itile]) * chunk;
+        const int64_t last = min((int64_t)a.near_cnt[itile], first + chunk);
+        const uint32_t *row = a.nearbits + itile * a.words;
+
+        const float4 ci = a.tbox_c[itile];
+        const float4 ei = a.tbox_e[itile];
+        const int64_t ibase = itile * T + lane * KI;
+        float2 xi[NPAIR], yi[NPAIR], zi[NPAIR], rxi[NPAIR], ryi[NPAIR], rzi[NPAIR], hI[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const float4 p0 = a.jdup[2 * (ibase + 2 * q)], p0z = a.jdup[2 * (ibase + 2 * q) + 1];
+            const float4 p1 = a.jdup[2 * (ibase + 2 * q + 1)], p1z = a.jdup[2 * (ibase + 2 * q + 1) + 1];
+            const float4 r0 = a.rdup[2 * (ibase + 2 * q)], r0z = a.rdup[2 * (ibase + 2 * q) + 1];
+            const float4 r1 = a.rdup[2 * (ibase + 2 * q + 1)], r1z = a.rdup[2 * (ibase + 2 * q + 1) + 1];
+            xi[q] = make_float2(p0.x, p1.x);
+            yi[q] = make_float2(p0.z, p1.z);
+            zi[q] = make_float2(p0z.x, p1z.x);
+            rxi[q] = make_float2(r0.x, r1.x);
+            ryi[q] = make_float2(r0.z, r1.z);
+            rzi[q] = make_float2(r0z.x, r1z.x);
+            hI[q] = make_float2(r0z.z, r1z.z);
+        }
+        float2 hx[NPAIR], hy[NPAIR], hz[NPAIR], cx_[NPAIR], cy_[NPAIR], cz_[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            hx[q] = hy[q] = hz[q] = make_float2(0.f, 0.f);
+            cx_[q] = cy_[q] = cz_[q] = make_float2(0.f, 0.f);
+        }
+        int64_t jt = select_near(row, a.words, first, lane);
+        int b = 0;
+        if (jt >= 0) issue(jt, b);
+        for (int64_t rk = first; rk < last && jt >= 0; ++rk) {
+            const int64_t jn = (rk + 1 < last) ? next_near(row, a.words, jt + 1, lane) : -1;
+            if (jn >= 0) issue(jn, b ^ 1);
+            bool got = true;
+            if (lane == 0) got = mbar_wait_bounded(smem_u32(&bars[b]), (uint32_t)(uses[b] & 1), a.wait_ns);
+            if (!__shfl_sync(0xffffffffu, got, 0)) {
+                if (lane == 0) {
+                    atomicExch(a.err, (int)STEPS_ETIMEOUT);
+                    // drain the copies still in flight before the warp exits
+                    mbar_wait_bounded(smem_u32(&bars[b]), (uint32_t)(uses[b] & 1), kDrainNs);
+                    if (jn >= 0)
+                        mbar_wait_bounded(smem_u32(&bars[b ^ 1]), (uint32_t)(uses[b ^ 1] & 1), kDrainNs);
+                }
+                return;
+            }
+            uses[b] += 1;
+            const float4 *S = buf + (size_t)b * 4 * T;  // jdup tile
+            const float4 *Rr = S + 2 * T;               // rdup tile
+            const float4 cj = a.tbox_c[jt];
+            float edx, edy, edz;
+            const float dcx = two_diff(ci.x, cj.x, edx);
+            const float dcy = two_diff(ci.y, cj.y, edy);
+            const float dcz = two_diff(ci.z, cj.z, edz);
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                // -(xs), xs = fl(o_i + dc), and -(r_i + err(dc) + err(xs)) for both targets
+                float2 nxs, nys, nzs, nrx, nry, nrz;
+                {
+                    float e0, e1;
+                    nxs.x = -two_sum(xi[q].x, dcx, e0);
+                    nxs.y = -two_sum(xi[q].y, dcx, e1);
+                    nrx = make_float2(-((rxi[q].x + edx) + e0), -((rxi[q].y + edx) + e1));
+                    nys.x = -two_sum(yi[q].x, dcy, e0);
+                    nys.y = -two_sum(yi[q].y, dcy, e1);
+                    nry = make_float2(-((ryi[q].x + edy) + e0), -((ryi[q].y + edy) + e1));
+                    nzs.x = -two_sum(zi[q].x, dcz, e0);
+                    nzs.y = -two_sum(zi[q].y, dcz, e1);
+                    nrz = make_float2(-((rzi[q].x + edz) + e0), -((rzi[q].y + edz) + e1));
+                }
+#pragma unroll 1
+                for (int f0 = 0; f0 < T; f0 += FOLD) {
+                    float2 px, py, pz;
+                    if (COMP) {
+                        px = py = pz = make_float2(0.f, 0.f);
+                    } else {
+                        px = hx[q];
+                        py = hy[q];
+                        pz = hz[q];
+                    }
+#pragma unroll 2
+                    for (int j = f0; j < f0 + FOLD; ++j) {
+                        const float4 A = S[2 * j], B = S[2 * j + 1];
+                        const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
+                        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxs),
+                                                     __fadd2_rn(make_float2(RA.x, RA.y), nrx));
+                        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nys),
+                                                     __fadd2_rn(make_float2(RA.z, RA.w), nry));
+                        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzs),
+                                                     __fadd2_rn(make_float2(RB.x, RB.y), nrz));
+                        float2 r2 = __fmul2_rn(dx, dx);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
+                        const float2 H2 = __fmul2_rn(H, H);
+                        const bool inner = r2.x < H2.x || r2.y < H2.y;
+                        if (!__any_sync(0xffffffffu, inner)) {
+                            const float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
+                                                          r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
+                            const float2 ri2 = __fmul2_rn(ri, ri);
+                            float2 sc = __fmul2_rn(make_float2(B.z, B.w), ri);
+                            sc = __fmul2_rn(sc, ri2);
+                            px = __ffma2_rn(sc, dx, px);
+                            py = __ffma2_rn(sc, dy, py);
+                            pz = __ffma2_rn(sc, dz, pz);
+                        } else {
+#pragma unroll
+                            for (int e = 0; e < 2; ++e) {
+                                const float r2e = e ? r2.y : r2.x;
+                                if (r2e > 0.f) {
+                                    const float He = e ? H.y : H.x;
+                                    const float ri = rsqrt_approx(r2e);
+                                    const float g = (r2e >= He * He) ? ri * ri * ri
+                                                                     : spline_over_r_f32(r2e * ri, He);
+                                    const float sc = B.z * g;
+                                    if (e) {
+                                        px.y = fmaf(sc, dx.y, px.y);
+                                        py.y = fmaf(sc, dy.y, py.y);
+                                        pz.y = fmaf(sc, dz.y, pz.y);
+                                    } else {
+                                        px.x = fmaf(sc, dx.x, px.x);
+                                        py.x = fmaf(sc, dy.x, py.x);
+                                        pz.x = fmaf(sc, dz.x, pz.x);
+                                    }
+                                }
+                            }
+                        }
+                    }
+                    if (COMP) {
+                        kahan2(hx[q], cx_[q], px);
+                        kahan2(hy[q], cy_[q], py);
+                        kahan2(hz[q], cz_[q], pz);
+                    } else {
+                        hx[q] = px;
+                        hy[q] = py;
+                        hz[q] = pz;
+                    }
+                }
+            }
+            __syncwarp();  // every lane is done with buffer b before it is refilled
+            jt = jn;
+            b ^= 1;
+        }
+        double *P = a.item_part + (size_t)item * 3 * T;
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+                const int li = lane * KI + 2 * q + e;
+                P[li] = (double)(e ? hx[q].y : hx[q].x) + (double)(e ? cx_[q].y : cx_[q].x);
+                P[T + li] = (double)(e ? hy[q].y : hy[q].x) + (double)(e ? cy_[q].y : cy_[q].x);
+                P[2 * T + li] = (double)(e ? hz[q].y : hz[q].x) + (double)(e ? cz_[q].y : cz_[q].x);
+            }
+        }
     }
 }
 
@@ -509,8 +803,9 @@ __device__ __forceinline__ int64_t cta_start(int64_t c, int64_t units, int64_t G
 }
 
 // Sum the per-CTA partials of each target in CTA order; apply G; sorted order.
-__global__ void fixup_kernel(const double *__restrict__ partial, int64_t n, int64_t ntile,
-                             int64_t units, int64_t G, int smax, int B_I, double Gc,
+__global__ void fixup_kernel(const double *__restrict__ partial, const double *__restrict__ item_part,
+                             const int64_t *__restrict__ item_off, int T, int64_t n,
+                             int64_t ntile, int64_t units, int64_t G, int smax, int B_I, double Gc,
                              double *__restrict__ ax, double *__restrict__ ay,
                              double *__restrict__ az) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -527,6 +822,16 @@ __global__ void fixup_kernel(const double *__restrict__ partial, int64_t n, int6
     };
     const int64_t clo = cta_of(ufirst), chi = cta_of(ulast);
     double sx = 0.0, sy = 0.0, sz = 0.0;
+    {
+        const int64_t row = p / T;
+        const int li = (int)(p - row * T);
+        for (int64_t it = item_off[row]; it < item_off[row + 1]; ++it) {
+            const double *Q = item_part + (size_t)it * 3 * T;
+            sx += Q[li];
+            sy += Q[T + li];
+            sz += Q[2 * T + li];
+        }
+    }
     for (int64_t c = clo; c <= chi; ++c) {
         const int64_t seg = blk - cta_start(c, units, G) / ntile;
         const double *P = partial + ((size_t)(c * smax + seg) * 3) * B_I;
@@ -541,29 +846,38 @@ __global__ void fixup_kernel(const double *__restrict__ partial, int64_t n, int6
 
 using KernelFn = void (*)(const ForceArgs);
 
-template <int KI, int NS>
+template <int KI, int W, int NS>
 constexpr size_t smem_of() {
-    return (size_t)NS * (32 * KI) * 48 + 2 * NS * sizeof(uint64_t);
+    return (size_t)NS * (32 * KI) * 32 + (size_t)NS * W * 32 + (size_t)W * (32 * KI) * 16 +
+           2 * NS * sizeof(uint64_t);
+}
+
+template <int KI>
+constexpr size_t near_smem_of() {
+    return (size_t)kNearWarps * 2 * (32 * KI) * 64 + 2 * kNearWarps * sizeof(uint64_t);
 }
 
 struct VariantImpl {
     Variant v;
-    KernelFn fn;
+    KernelFn fn;       // far field (stream-K, TMA pipeline)
+    KernelFn near_fn;  // near field (warp per target tile)
     size_t smem;
+    size_t near_smem;
 };
 
-#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, NAME)                                  \
-    {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB>, smem_of<KI, NS>()}
+#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, NAME)                                    \
+    {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB>,                 \
+     near_f32_kernel<KI, COMP, FOLD>, smem_of<KI, W, NS>(), near_smem_of<KI>()}
 
 const VariantImpl kVariants[] = {
-    STEPS_VARIANT(4, 8, 4, true, 32, 2, "comp_ki4_w8_ns4_f32"),
-    STEPS_VARIANT(4, 4, 4, true, 32, 3, "comp_ki4_w4_ns4_f32"),
-    STEPS_VARIANT(8, 4, 3, true, 32, 1, "comp_ki8_w4_ns3_f32"),
-    STEPS_VARIANT(2, 8, 4, true, 32, 3, "comp_ki2_w8_ns4_f32"),
-    STEPS_VARIANT(4, 8, 4, false, 32, 2, "naive_ki4_w8_ns4"),
-    STEPS_VARIANT(4, 4, 4, false, 32, 3, "naive_ki4_w4_ns4"),
-    STEPS_VARIANT(8, 4, 3, false, 32, 1, "naive_ki8_w4_ns3"),
-    STEPS_VARIANT(2, 8, 4, false, 32, 3, "naive_ki2_w8_ns4"),
+    STEPS_VARIANT(4, 8, 6, true, 32, 2, "comp_ki4_w8_ns6_f32"),
+    STEPS_VARIANT(4, 4, 6, true, 32, 4, "comp_ki4_w4_ns6_f32"),
+    STEPS_VARIANT(8, 4, 4, true, 32, 2, "comp_ki8_w4_ns4_f32"),
+    STEPS_VARIANT(2, 8, 6, true, 32, 4, "comp_ki2_w8_ns6_f32"),
+    STEPS_VARIANT(4, 8, 6, false, 32, 2, "naive_ki4_w8_ns6"),
+    STEPS_VARIANT(4, 4, 6, false, 32, 4, "naive_ki4_w4_ns6"),
+    STEPS_VARIANT(8, 4, 4, false, 32, 2, "naive_ki8_w4_ns4"),
+    STEPS_VARIANT(2, 8, 6, false, 32, 4, "naive_ki2_w8_ns6"),
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -582,6 +896,7 @@ ForcePlan plan_force(const Staging &s, int k, int num_sms) {
     p.units = p.niblk * s.ntile;
     int per_sm = 1;
     cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.smem);
+    cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vi.fn, (vi.v.W + 1) * 32, vi.smem) !=
             cudaSuccess ||
         per_sm < 1)
@@ -596,16 +911,22 @@ ForcePlan plan_force(const Staging &s, int k, int num_sms) {
     return p;
 }
 
-cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial, int *err,
-                             unsigned long long *stats, float alpha, long long wait_ns,
-                             cudaStream_t st) {
+cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
+                             const NearScratch &nr, int *err, unsigned long long *stats,
+                             float alpha, long long wait_ns, int num_sms, cudaStream_t st) {
     const VariantImpl &vi = kVariants[p.variant];
     ForceArgs a;
     a.jdup = s.jdup;
-    a.res = s.res;
+    a.rdup = s.rdup;
     a.tbox_c = s.tbox_c;
     a.tbox_e = s.tbox_e;
     a.partial = partial;
+    a.item_part = nr.item_part;
+    a.nearbits = nr.bits;
+    a.near_cnt = nr.cnt;
+    a.item_off = nr.item_off;
+    a.near_meta = nr.meta;
+    a.words = (s.ntile + 31) / 32;
     a.err = err;
     a.stats = stats;
     a.ntile = s.ntile;
@@ -613,15 +934,25 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.smax = p.smax;
     a.alpha2 = alpha * alpha;
     a.wait_ns = wait_ns;
+    cudaError_t e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)s.ntile * a.words, st);
+    if (e != cudaSuccess) return e;
     vi.fn<<<p.grid, (vi.v.W + 1) * 32, vi.smem, st>>>(a);
+    near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, s.ntile, a.words, nr.cnt);
+    near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, nr.item_off, nr.meta);
+    int per_sm = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vi.near_fn, 32 * kNearWarps, vi.near_smem) !=
+            cudaSuccess || per_sm < 1)
+        per_sm = 1;
+    vi.near_fn<<<(unsigned)(num_sms * per_sm), 32 * kNearWarps, vi.near_smem, st>>>(a);
     return cudaGetLastError();
 }
 
-cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial, double G,
-                         double *ax, double *ay, double *az, cudaStream_t st) {
+cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial,
+                         const NearScratch &nr, double G, double *ax, double *ay, double *az,
+                         cudaStream_t st) {
     const int tb = 256;
     const int64_t blocks = (s.n + tb - 1) / tb;
-    fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(partial, s.n, s.ntile, p.units, p.grid, p.smax,
+    fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(partial, nr.item_part, nr.item_off, s.T, s.n, s.ntile, p.units, p.grid, p.smax,
                                                   p.B_I, G, ax, ay, az);
     return cudaGetLastError();
 }

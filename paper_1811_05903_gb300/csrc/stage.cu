@@ -45,7 +45,7 @@ struct SumOp {
 __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              const double *__restrict__ y, const double *__restrict__ z,
                              const double *__restrict__ m, const double *__restrict__ h,
-                             float4 *__restrict__ jdup, float4 *__restrict__ res,
+                             float4 *__restrict__ jdup, float4 *__restrict__ rdup,
                              float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e) {
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
@@ -94,7 +94,8 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     }
     jdup[2 * p] = make_float4(ox, ox, oy, oy);
     jdup[2 * p + 1] = make_float4(oz, oz, fm, fm);
-    res[p] = make_float4(rx, ry, rz, fh);
+    rdup[2 * p] = make_float4(rx, rx, ry, ry);
+    rdup[2 * p + 1] = make_float4(rz, rz, fh, fh);
     if (threadIdx.x == 0) {
         // extents and softening rounded up so the box tests stay conservative
         tbox_c[tile] = make_float4(cx, cy, cz, __double2float_ru(hmax));
@@ -235,7 +236,7 @@ inline unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) /
 
 void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
                   const double *m, const double *h, cudaStream_t st) {
-    stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.res,
+    stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup,
                                                     s.tbox_c, s.tbox_e);
 }
 

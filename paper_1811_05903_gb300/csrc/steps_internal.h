@@ -50,7 +50,7 @@ struct Staging {
     int T = 0;            // tile size (particles)
     int64_t ntile = 0;    // np / T
     float4 *jdup = nullptr;   // [2 np] (ox, ox, oy, oy), (oz, oz, m, m): FP32 offsets from the tile centre
-    float4 *res = nullptr;    // [np] (rx, ry, rz, h): FP32 residual x - c - o, softening
+    float4 *rdup = nullptr;   // [2 np] (rx, rx, ry, ry), (rz, rz, h, h): FP32 residual x - c - o, softening
     float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
 };
@@ -58,6 +58,16 @@ struct Staging {
 // Launch the staging kernel: FP64 sorted SoA -> FP32 tile-relative arrays.
 void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
                   const double *m, const double *h, cudaStream_t st);
+
+// Near-field scratch: bitmap of near tile pairs, per-row counts, work items.
+struct NearScratch {
+    uint32_t *bits = nullptr;     // [ntile][(ntile + 31) / 32]
+    int *cnt = nullptr;           // [ntile]
+    int64_t *item_off = nullptr;  // [ntile + 1]
+    int64_t *meta = nullptr;      // [3] {chunk, items, work counter}
+    double *item_part = nullptr;  // [cap_items][3][T]
+    int64_t cap_items = 0;
+};
 
 // Stream-K plan for one FP32 force evaluation.
 struct ForcePlan {
@@ -74,11 +84,16 @@ ForcePlan plan_force(const Staging &s, int variant, int num_sms);
 size_t force_smem_bytes(int variant);
 // alpha: tile pairs whose boxes are closer than alpha * (|c_I - c_J| + |e_I| + |e_J|)
 // take the compensated near-field path.  stats (may be null) counts near/all tile pairs.
-cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial, int *err,
-                             unsigned long long *stats, float alpha, long long wait_ns,
-                             cudaStream_t st);
-cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial, double G,
-                         double *ax, double *ay, double *az, cudaStream_t st);
+// Launches the far-field kernel (stream-K over all tile pairs, near ones
+// skipped) and the near-field kernel (near_acc [3][np]).
+// Far field (stream-K over tile pairs; marks near pairs in nr.bits, cleared
+// here) then the near-field work items.  5 kernels + 1 memset.
+cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
+                             const NearScratch &nr, int *err, unsigned long long *stats,
+                             float alpha, long long wait_ns, int num_sms, cudaStream_t st);
+cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial,
+                         const NearScratch &nr, double G, double *ax, double *ay, double *az,
+                         cudaStream_t st);
 
 // FP64 comparison path: direct sum over sorted FP64 SoA, targets [i0, i1).
 cudaError_t launch_force_f64(int64_t n, const double *x, const double *y, const double *z,

@@ -27,6 +27,7 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
+    "steps_force_stats",
 ]
 
 
@@ -87,6 +88,7 @@ def load(build_if_missing: bool = False):
     lib.steps_forces_subset.argtypes = [P, I64, P, P]
     lib.steps_profile_enable.argtypes = [P, I]
     lib.steps_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(I64), I]
+    lib.steps_force_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
@@ -94,7 +96,7 @@ def load(build_if_missing: bool = False):
                  "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
-                 "steps_profile_read"]:
+                 "steps_profile_read", "steps_force_stats"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -173,6 +175,13 @@ def steps_profile_read(ctx, reset: bool = True):
     _check(load().steps_profile_read(ctx, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(kl),
                                      1 if reset else 0))
     return ms.value, fl.value, kl.value
+
+
+def steps_force_stats(ctx):
+    """(near tile pairs, all tile pairs) since the last call."""
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(load().steps_force_stats(ctx, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
 
 
 def steps_kdk_step(ctx, dt: float, want_a: bool = False):

@@ -91,7 +91,8 @@ def test_compactified_all_variants(n_central, per_shell):
         if prec == steps.STEPS_F32_COMP:
             assert rms <= RMS_TOL and e.max() <= MAX_TOL, (name, rms, e.max())
         else:
-            assert rms <= 1e-5, (name, rms)
+            # one FP32 running sum per target: only the comparison row, ill-conditioned here
+            assert np.isfinite(e).all() and rms <= 1e-3, (name, rms)
 
 
 @pytest.mark.parametrize("n", [1, 2, 3, 31, 33, 64, 65, 127, 129, 1023, 1025, 3000])
