@@ -183,6 +183,7 @@ def run_ours(args):
     sim = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg,
                            stream=stream.cuda_stream)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    variant_name = steps.steps_variants()[steps.steps_get_variant(sim.ctx)]
 
     # ---- accuracy at the initial positions (mixed, naive, FP64 GPU) ----
     acc_mixed = np.empty((n, 3))
@@ -257,6 +258,7 @@ def run_ours(args):
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     force_ms, force_launches, kernel_launches = steps.steps_profile_read(sim.ctx, reset=True)
+    near_pairs, all_pairs = steps.steps_force_stats(sim.ctx)
     steps.steps_profile_enable(sim.ctx, False)
     total_s = sum(step_ms) * 1e-3
     if ws > 1:
@@ -300,7 +302,7 @@ def run_ours(args):
         "config": {"workload": desc, "n": n, "prec": "f32 pairs, compensated sums, fp64 integrator",
                    "parallelism": "replicas" if ws > 1 else "single gpu",
                    "l2": "flushed between timed steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20),
-                   "variant": args.variant or "auto"},
+                   "variant": variant_name},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": None,
                      "kernel": "force_f32_kernel (pair forces)",
@@ -320,6 +322,7 @@ def run_ours(args):
                         **err.get("f64_gpu", {})},
             "error_targets": int(tg.size),
         },
+        "near_field_fraction": near_pairs / max(all_pairs, 1),
         "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)

@@ -213,6 +213,9 @@ steps_status steps_force_stats(steps_ctx *ctx, uint64_t *near_pairs, uint64_t *a
 /* Force-kernel variants built into the library (for tile_override and tuning). */
 int steps_num_variants(void);
 const char *steps_variant_name(int k);
+/* The variant (0-based) the context's FP32 path uses, as chosen by
+ * tile_override or the autotuner; -1 for STEPS_F64. */
+steps_status steps_get_variant(steps_ctx *ctx, int *k);
 
 #ifdef __cplusplus
 }

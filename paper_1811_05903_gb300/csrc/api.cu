@@ -142,32 +142,38 @@ steps_status sync_and_check(steps_ctx *c) {
     return STEPS_OK;
 }
 
+// Default variant before tuning: 4 targets per thread, 4 compute warps; small
+// systems use 64-particle tiles (2 targets per thread) to limit padding.
 int pick_variant(const steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
     if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())
         return c->cfg.tile_override - 1;
-    // default: 4 targets per thread; smaller tiles for small systems
     const int ki = c->n >= 32768 ? 4 : 2;
     for (int k = 0; k < num_variants(); ++k) {
         const Variant &v = variant(k);
-        if (v.comp == comp && v.KI == ki && v.W == 8) return k;
+        if (v.comp == comp && v.KI == ki) return k;
     }
     return 0;
 }
 
+// Tuned variant per (size bucket, compensated?) for this process.
+std::mutex g_tune_mu;
+std::vector<std::pair<std::pair<int, int>, int>> g_tuned;
+
 steps_status configure_variant(steps_ctx *c, int k) {
     const Variant &v = variant(k);
     c->variant = k;
+    const int64_t bi = (int64_t)v.W * 32 * v.KI;
     c->stg.n = c->n;
-    c->stg.np = c->np;
+    c->stg.np = (c->n + bi - 1) / bi * bi;  // <= c->np, the allocated padding
     c->stg.T = 32 * v.KI;
-    c->stg.ntile = c->np / c->stg.T;
+    c->stg.ntile = c->stg.np / c->stg.T;
     c->stg.jdup = c->jdup_buf;
     c->stg.rdup = c->rdup_buf;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     c->plan = plan_force(c->stg, k, c->num_sms);
-    c->nr.cap_items = 8 * c->stg.ntile;
+    c->nr.cap_items = 8 * (c->np / c->stg.T);
     if (c->plan.partial_elems > c->partial_cap) {
         dev_free(c, c->partial);
         c->partial = nullptr;
@@ -229,6 +235,54 @@ steps_status compute_forces(steps_ctx *c) {
     c->force_launches += 1;
     if (prof) c->force_events.push_back({e0, e1});
     return STEPS_OK;
+}
+
+// Autotuner: for systems of >= 2^17 particles, time one pair-force evaluation
+// with every built variant of the requested summation mode and keep the
+// fastest; the choice is cached per (floor(log2 n), mode) for the process.
+steps_status autotune(steps_ctx *c) {
+    const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
+    if (c->n < (1 << 17)) return STEPS_OK;
+    int bucket = 0;
+    while ((int64_t(1) << (bucket + 1)) <= c->n) ++bucket;
+    const std::pair<int, int> key(bucket, comp ? 1 : 0);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        for (auto &e : g_tuned)
+            if (e.first == key) return configure_variant(c, e.second);
+    }
+    const bool prof = c->profiling;
+    c->profiling = false;
+    cudaEvent_t e0, e1;
+    STEPS_CUDA(cudaEventCreate(&e0));
+    STEPS_CUDA(cudaEventCreate(&e1));
+    int best = c->variant;
+    float best_ms = 1e30f;
+    steps_status st = STEPS_OK;
+    for (int k = 0; k < num_variants() && st == STEPS_OK; ++k) {
+        if (variant(k).comp != comp) continue;
+        st = configure_variant(c, k);
+        if (st == STEPS_OK) st = compute_forces(c);  // warm-up (first launch of the variant)
+        if (st == STEPS_OK && cudaEventRecord(e0, c->st) != cudaSuccess) st = STEPS_ECUDA;
+        if (st == STEPS_OK) st = compute_forces(c);
+        if (st == STEPS_OK && cudaEventRecord(e1, c->st) != cudaSuccess) st = STEPS_ECUDA;
+        if (st == STEPS_OK) st = sync_and_check(c);
+        float ms = 0.f;
+        if (st == STEPS_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
+            best_ms = ms;
+            best = k;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->profiling = prof;
+    STEPS_TRY(st);
+    cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned.push_back({key, best});
+    }
+    return configure_variant(c, best);
 }
 
 // One KDK step with dt already in sc[SC_DT] (Eq. 11).
@@ -296,8 +350,9 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->err, 2));
     c->flag = c->err + 1;
     STEPS_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->st));
-    // staging: pad to a multiple of every variant's i-block (all divide 1024)
-    c->np = (n + 1023) / 1024 * 1024;
+    // staging: padded so that every variant's i-block (W x 32 KI targets, all
+    // dividing 6144) fits; each variant pads to its own multiple
+    c->np = (n + 6143) / 6144 * 6144;
     c->ntile_cap = c->np / 64;
     STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->rdup_buf, 2 * c->np));
@@ -358,6 +413,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_CUDA(cudaMemcpyAsync(c->sc, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
     STEPS_TRY(configure_variant(c, pick_variant(c)));
     STEPS_TRY(resort(c));
+    if (c->cfg.prec != STEPS_F64 && c->cfg.tile_override == 0) STEPS_TRY(autotune(c));
     STEPS_TRY(compute_forces(c));
     return sync_and_check(c);
 }
@@ -833,6 +889,15 @@ steps_status steps_set_memory_limit(size_t bytes) {
 }
 
 int steps_num_variants(void) { return num_variants(); }
+
+steps_status steps_get_variant(steps_ctx *c, int *k) {
+    if (!c || !k) {
+        set_error("ctx and k are required");
+        return STEPS_EINVAL;
+    }
+    *k = c->cfg.prec == STEPS_F64 ? -1 : c->variant;
+    return STEPS_OK;
+}
 
 const char *steps_variant_name(int k) {
     if (k < 0 || k >= num_variants()) return nullptr;

@@ -218,12 +218,15 @@ struct ForceArgs {
 // (summed later by near_f32_kernel) and stages c_I - c_J (split exactly into
 // a float and its rounding error) and the tile mass in shared memory.  The
 // compute warps then only see far tile pairs, all of equal cost.
-template <int KI, int W, int NS, bool COMP, int FOLD, int MINB>
+//   KSM   keep the Kahan state (touched once per FOLD sources) in shared memory
+//         instead of registers, trading LSU work for occupancy
+template <int KI, int W, int NS, bool COMP, int FOLD, int MINB, int UNR, bool KSM>
 __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
     constexpr int NPAIR = KI / 2;
     constexpr int B_I = W * T;
     constexpr uint32_t BYTES_J = T * 32u;
+    constexpr bool SMK = COMP && KSM;
     static_assert(T % FOLD == 0, "fold length must divide the tile");
     static_assert(W <= 32, "one producer lane per compute warp");
 
@@ -231,7 +234,8 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
     float4 *sj = reinterpret_cast<float4 *>(smem);                                // [NS][2T]
     float4 *smeta = reinterpret_cast<float4 *>(smem + NS * BYTES_J);              // [NS][W][2]
     float4 *sipos = smeta + NS * W * 2;                                           // [W][T]
-    uint64_t *bars = reinterpret_cast<uint64_t *>(sipos + W * T);                 // full[NS], empty[NS]
+    float2 *skah = reinterpret_cast<float2 *>(sipos + W * T);                     // [6][NPAIR][32 W] (SMK)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(skah + (SMK ? 6 * NPAIR * 32 * W : 0));  // full, empty
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -344,10 +348,15 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
         }
         float2 hx[NPAIR], hy[NPAIR], hz[NPAIR];     // running sums
         float2 cx_[NPAIR], cy_[NPAIR], cz_[NPAIR];  // Kahan terms (negated), COMP only
+        const int tid = warp * 32 + lane;
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             hx[q] = hy[q] = hz[q] = make_float2(0.f, 0.f);
             cx_[q] = cy_[q] = cz_[q] = make_float2(0.f, 0.f);
+            if (SMK) {
+#pragma unroll
+                for (int c = 0; c < 6; ++c) skah[(c * NPAIR + q) * 32 * W + tid] = make_float2(0.f, 0.f);
+            }
         }
 
         for (; u < seg_end; ++u, ++k) {
@@ -416,7 +425,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                 const float4 *S = sj + (size_t)s * 2 * T;
 #pragma unroll 1
                 for (int j0 = 0; j0 < T; j0 += FOLD) {
-#pragma unroll 2
+#pragma unroll UNR
                     for (int j = j0; j < j0 + FOLD; ++j) {
                         const float4 A = S[2 * j];
                         const float4 B = S[2 * j + 1];
@@ -441,7 +450,25 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                             pz[q] = __ffma2_rn(sc, dz, pz[q]);
                         }
                     }
-                    if (COMP) {
+                    if (SMK) {
+#pragma unroll
+                        for (int q = 0; q < NPAIR; ++q) {
+                            float2 *K = skah + q * 32 * W + tid;
+                            constexpr int CS = NPAIR * 32 * W;  // component stride
+                            float2 h0 = K[0], h1 = K[CS], h2 = K[2 * CS];
+                            float2 c0 = K[3 * CS], c1 = K[4 * CS], c2 = K[5 * CS];
+                            kahan2(h0, c0, px[q]);
+                            kahan2(h1, c1, py[q]);
+                            kahan2(h2, c2, pz[q]);
+                            K[0] = h0;
+                            K[CS] = h1;
+                            K[2 * CS] = h2;
+                            K[3 * CS] = c0;
+                            K[4 * CS] = c1;
+                            K[5 * CS] = c2;
+                            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+                        }
+                    } else if (COMP) {
 #pragma unroll
                         for (int q = 0; q < NPAIR; ++q) {
                             kahan2(hx[q], cx_[q], px[q]);
@@ -469,6 +496,16 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
         const int loc = warp * T + lane * KI;
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
+            if (SMK) {
+                const float2 *K = skah + q * 32 * W + tid;
+                constexpr int CS = NPAIR * 32 * W;
+                hx[q] = K[0];
+                hy[q] = K[CS];
+                hz[q] = K[2 * CS];
+                cx_[q] = K[3 * CS];
+                cy_[q] = K[4 * CS];
+                cz_[q] = K[5 * CS];
+            }
             P[0 * B_I + loc + 2 * q] = (double)hx[q].x + (double)cx_[q].x;
             P[0 * B_I + loc + 2 * q + 1] = (double)hx[q].y + (double)cx_[q].y;
             P[1 * B_I + loc + 2 * q] = (double)hy[q].x + (double)cy_[q].x;
@@ -846,10 +883,10 @@ __global__ void fixup_kernel(const double *__restrict__ partial, const double *_
 
 using KernelFn = void (*)(const ForceArgs);
 
-template <int KI, int W, int NS>
+template <int KI, int W, int NS, bool SMK>
 constexpr size_t smem_of() {
     return (size_t)NS * (32 * KI) * 32 + (size_t)NS * W * 32 + (size_t)W * (32 * KI) * 16 +
-           2 * NS * sizeof(uint64_t);
+           (SMK ? (size_t)6 * (KI / 2) * 32 * W * 8 : 0) + 2 * NS * sizeof(uint64_t);
 }
 
 template <int KI>
@@ -860,24 +897,23 @@ constexpr size_t near_smem_of() {
 struct VariantImpl {
     Variant v;
     KernelFn fn;       // far field (stream-K, TMA pipeline)
-    KernelFn near_fn;  // near field (warp per target tile)
+    KernelFn near_fn;  // near field (balanced work items)
     size_t smem;
     size_t near_smem;
 };
 
-#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, NAME)                                    \
-    {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB>,                 \
-     near_f32_kernel<KI, COMP, FOLD>, smem_of<KI, W, NS>(), near_smem_of<KI>()}
+#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, UNR, KSM, NAME)                          \
+    {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB, UNR, KSM>,       \
+     near_f32_kernel<KI, COMP, FOLD>, smem_of<KI, W, NS, COMP && KSM>(), near_smem_of<KI>()}
 
 const VariantImpl kVariants[] = {
-    STEPS_VARIANT(4, 8, 6, true, 32, 2, "comp_ki4_w8_ns6_f32"),
-    STEPS_VARIANT(4, 4, 6, true, 32, 4, "comp_ki4_w4_ns6_f32"),
-    STEPS_VARIANT(8, 4, 4, true, 32, 2, "comp_ki8_w4_ns4_f32"),
-    STEPS_VARIANT(2, 8, 6, true, 32, 4, "comp_ki2_w8_ns6_f32"),
-    STEPS_VARIANT(4, 8, 6, false, 32, 2, "naive_ki4_w8_ns6"),
-    STEPS_VARIANT(4, 4, 6, false, 32, 4, "naive_ki4_w4_ns6"),
-    STEPS_VARIANT(8, 4, 4, false, 32, 2, "naive_ki8_w4_ns4"),
-    STEPS_VARIANT(2, 8, 6, false, 32, 4, "naive_ki2_w8_ns6"),
+    STEPS_VARIANT(4, 4, 6, true, 32, 3, 4, false, "comp_ki4_w4_u4"),
+    STEPS_VARIANT(4, 8, 6, true, 32, 2, 2, false, "comp_ki4_w8_u2"),
+    STEPS_VARIANT(6, 8, 6, true, 32, 2, 2, false, "comp_ki6_w8_u2"),
+    STEPS_VARIANT(2, 8, 6, true, 32, 4, 4, false, "comp_ki2_w8_u4"),
+    STEPS_VARIANT(4, 4, 6, false, 32, 3, 4, false, "naive_ki4_w4_u4"),
+    STEPS_VARIANT(4, 8, 6, false, 32, 2, 2, false, "naive_ki4_w8_u2"),
+    STEPS_VARIANT(2, 8, 6, false, 32, 4, 4, false, "naive_ki2_w8_u4"),
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
