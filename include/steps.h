@@ -202,6 +202,16 @@ steps_status steps_profile_enable(steps_ctx *ctx, int on);
 steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force_launches,
                                 int64_t *kernel_launches, int reset);
 
+
+/*
+ * Near-field threshold of the FP32 path (default 1/32): a source tile is
+ * summed with the compensated near-field method when its bounding box comes
+ * closer to the target tile than alpha x (centre distance + both extents);
+ * pairs inside h_i + h_j and tiles larger than their distance always are.
+ * Larger alpha moves more work to the (slower, more exact) near field.
+ */
+steps_status steps_set_near_alpha(steps_ctx *ctx, double alpha);
+
 /*
  * Tile-pair statistics of the FP32 path since the last call (reset on read):
  * how many target-tile x source-tile pairs were classified near field

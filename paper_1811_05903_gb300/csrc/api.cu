@@ -793,6 +793,15 @@ steps_status steps_forces_subset(steps_ctx *c, int64_t nt, const int64_t *target
     return s;
 }
 
+steps_status steps_set_near_alpha(steps_ctx *c, double alpha) {
+    if (!c || !(alpha >= 0.0) || !std::isfinite(alpha)) {
+        set_error("ctx is NULL or alpha is negative or not finite");
+        return STEPS_EINVAL;
+    }
+    c->alpha = (float)alpha;
+    return STEPS_OK;
+}
+
 steps_status steps_profile_enable(steps_ctx *c, int on) {
     if (!c) {
         set_error("ctx is NULL");

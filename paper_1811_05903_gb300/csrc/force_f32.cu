@@ -163,13 +163,15 @@ __device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
     hi = t;
 }
 
-// Tile-pair classification shared by the far-field and near-field kernels.
-// Both kernels must reach the same decision for every pair, so the test uses
-// explicitly rounded operations (no contraction into FMAs).  Conservative
-// margins of 2^-18 cover the FP32 rounding of the box arithmetic.
+// Tile-pair classification (done once per pair by the far-field producer;
+// the near-field kernel reads the resulting bitmap).  Conservative margins of
+// 2^-18 cover the FP32 rounding of the box arithmetic.
 //  * near if some pair may be closer than h_i + h_j (spline branches of Eq. 4);
 //  * near if the boxes are closer than alpha x (|c_I - c_J| + |e_I| + |e_J|),
-//    where one FP32 difference of offsets could lose relative precision in d.
+//    where one FP32 difference of offsets could lose relative precision in d;
+//  * near if |e_I| + |e_J| > |c_I - c_J|: the far field's first-order
+//    correction of the target shift uses the source tile's monopole tidal
+//    tensor, which needs the tiles to be smaller than their distance.
 __device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei, const float4 cj,
                                                const float4 ej, const float alpha2) {
     const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
@@ -183,7 +185,10 @@ __device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei,
     const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dcx, dcx), __fmul_rn(dcy, dcy)), __fmul_rn(dcz, dcz));
     const float ni = __fadd_rn(__fadd_rn(__fmul_rn(ei.x, ei.x), __fmul_rn(ei.y, ei.y)), __fmul_rn(ei.z, ei.z));
     const float nj = __fadd_rn(__fadd_rn(__fmul_rn(ej.x, ej.x), __fmul_rn(ej.y, ej.y)), __fmul_rn(ej.z, ej.z));
-    const float scale = __fadd_rn(__fadd_rn(__fsqrt_rn(n2), __fsqrt_rn(ni)), __fsqrt_rn(nj));
+    const float dist = __fsqrt_rn(n2);
+    const float ext = __fadd_rn(__fsqrt_rn(ni), __fsqrt_rn(nj));
+    if (__fmul_rn(ext, up) > dist) return true;
+    const float scale = __fadd_rn(dist, ext);
     return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
 }
 
@@ -537,6 +542,11 @@ __device__ __forceinline__ int64_t next_near(const uint32_t *__restrict__ row, i
 
 constexpr int kNearWarps = 4;   // warps per CTA of the near-field kernel
 constexpr int kNearChunk = 32;  // near tiles per work item (raised on device if needed)
+// Near-field sources per compensated fold.  Neighbouring tiles contribute
+// nearly parallel pair forces whose FP32 partial sums grow coherently; the
+// rounding error of such a sum grows with its length, so the near field folds
+// more often than the far field (it is a small share of the work).
+constexpr int kNearFold = 8;
 
 // Rank-th set bit (0-based) of a bitmap row, or -1; warp-cooperative.
 __device__ __forceinline__ int64_t select_near(const uint32_t *__restrict__ row, int64_t words,
@@ -904,7 +914,7 @@ struct VariantImpl {
 
 #define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, UNR, KSM, NAME)                          \
     {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB, UNR, KSM>,       \
-     near_f32_kernel<KI, COMP, FOLD>, smem_of<KI, W, NS, COMP && KSM>(), near_smem_of<KI>()}
+     near_f32_kernel<KI, COMP, kNearFold>, smem_of<KI, W, NS, COMP && KSM>(), near_smem_of<KI>()}
 
 const VariantImpl kVariants[] = {
     STEPS_VARIANT(4, 4, 6, true, 32, 3, 4, false, "comp_ki4_w4_u4"),

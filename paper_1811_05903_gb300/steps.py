@@ -27,7 +27,7 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
-    "steps_force_stats", "steps_get_variant",
+    "steps_force_stats", "steps_get_variant", "steps_set_near_alpha",
 ]
 
 
@@ -90,6 +90,7 @@ def load(build_if_missing: bool = False):
     lib.steps_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(I64), I]
     lib.steps_force_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_get_variant.argtypes = [P, ctypes.POINTER(I)]
+    lib.steps_set_near_alpha.argtypes = [P, D]
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
@@ -97,7 +98,8 @@ def load(build_if_missing: bool = False):
                  "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
-                 "steps_profile_read", "steps_force_stats", "steps_get_variant"]:
+                 "steps_profile_read", "steps_force_stats", "steps_get_variant",
+                 "steps_set_near_alpha"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -242,6 +244,10 @@ def steps_set_wait_limit(ctx, ns: int):
 
 def steps_set_memory_limit(nbytes: int):
     _check(load().steps_set_memory_limit(int(nbytes)))
+
+
+def steps_set_near_alpha(ctx, alpha: float):
+    _check(load().steps_set_near_alpha(ctx, float(alpha)))
 
 
 def steps_get_variant(ctx) -> int:
