@@ -202,6 +202,34 @@ steps_status steps_profile_enable(steps_ctx *ctx, int on);
 steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force_launches,
                                 int64_t *kernel_launches, int reset);
 
+/*
+ * steps_forces_noalloc -- the pair term of Eq. 8 (same definition and FP32
+ * compensated arithmetic as steps_forces) for a system of at most
+ * STEPS_NOALLOC_MAX_N particles, without allocating any device memory.  The
+ * paper has no counterpart: this entry point exists for callers that cannot
+ * allocate around a force evaluation, e.g. code running inside an application
+ * whose caching allocator already owns the device memory, or a per-step loop
+ * that must not take the implicit device synchronisation of cudaMalloc and
+ * cudaFree.  All scratch lives in one fixed array of about 6.7 MiB compiled
+ * into this library; every device that loads the library holds it until exit.
+ *   pos [n][3], mass [n], soft [n] (or NULL: Eq. 7 with h_min), acc_out [n][3]:
+ *   device pointers on the current device, caller order, caller-owned.
+ *   cuda_stream: stream to run on (NULL = legacy default stream); the call
+ *   synchronises it before returning.
+ * Errors: EINVAL for n outside [1, STEPS_NOALLOC_MAX_N] (checked before any
+ * GPU work), NULL or host pointers, or non-finite / non-positive inputs;
+ * ECUDA; ETIMEOUT as for steps_forces.
+ * The first call on a device looks up the scratch array's device address and
+ * caches it; make that first call before capturing a stream into a graph.
+ * Every call shares the scratch array, which keeps the previous call's
+ * contents (the call clears what must start at zero): calls that overlap on
+ * the GPU -- different streams or host threads on one device -- race and must
+ * be serialised by the caller.
+ */
+#define STEPS_NOALLOC_MAX_N 8192
+steps_status steps_forces_noalloc(int64_t n, const double *pos, const double *mass,
+                                  const double *soft, double h_min, double G, double *acc_out,
+                                  void *cuda_stream);
 
 /*
  * Near-field threshold of the FP32 path (default 1/32): a source tile is

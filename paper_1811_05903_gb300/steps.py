@@ -27,7 +27,7 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
-    "steps_force_stats", "steps_get_variant", "steps_set_near_alpha",
+    "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
 ]
 
 
@@ -91,6 +91,7 @@ def load(build_if_missing: bool = False):
     lib.steps_force_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_get_variant.argtypes = [P, ctypes.POINTER(I)]
     lib.steps_set_near_alpha.argtypes = [P, D]
+    lib.steps_forces_noalloc.argtypes = [I64, P, P, P, D, D, P, P]
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
@@ -99,7 +100,7 @@ def load(build_if_missing: bool = False):
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
                  "steps_profile_read", "steps_force_stats", "steps_get_variant",
-                 "steps_set_near_alpha"]:
+                 "steps_forces_noalloc", "steps_set_near_alpha"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -244,6 +245,18 @@ def steps_set_wait_limit(ctx, ns: int):
 
 def steps_set_memory_limit(nbytes: int):
     _check(load().steps_set_memory_limit(int(nbytes)))
+
+
+STEPS_NOALLOC_MAX_N = 8192
+
+
+def steps_forces_noalloc(pos, mass, acc_out, soft=None, h_min=0.0, G=1.0, stream=None):
+    """Pair term for <= STEPS_NOALLOC_MAX_N particles with no device allocation.
+    pos/mass/soft/acc_out are device tensors (float64, contiguous)."""
+    n = int(mass.shape[0])
+    _check(load().steps_forces_noalloc(n, ptr(pos), ptr(mass), ptr(soft), float(h_min), float(G),
+                                       ptr(acc_out), stream))
+    return acc_out
 
 
 def steps_set_near_alpha(ctx, alpha: float):
