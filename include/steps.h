@@ -232,6 +232,37 @@ steps_status steps_forces_noalloc(int64_t n, const double *pos, const double *ma
                                   void *cuda_stream);
 
 /*
+ * Ensembles: many independent simulations of uneven N and differing
+ * cosmologies advanced together (batched runs for parameter studies, the use
+ * the paper names for fast low-resolution simulations).  Each member is
+ * a system of its own -- its particles interact only with each other -- with
+ * its own steps_config (G, H0, Om, OL, Or, Ok, mode; precision, re-sort period
+ * and tile_override are taken from cfgs[0]), t0, a0 and softening (soft[s], or
+ * NULL / soft == NULL: Eq. 7 with h_min[s]).  All members share one force
+ * launch per step (the far-field grid walks every member's tile pairs) and
+ * one CUDA graph per step.
+ *   n [nsims], pos/vel/mass/soft: arrays of nsims pointers (host or device),
+ *   each [n_s][3] or [n_s] in the member's caller order; vel may be NULL.
+ * steps_ensemble_run: nsteps KDK steps (Eq. 9-11), dts [nsims][nsteps] host,
+ * row-major (member s uses dts[s*nsteps + k] at step k).
+ * steps_ensemble_get_state: member s's state in its caller order (any output
+ * pointer may be NULL).  steps_ensemble_stats: padded particle total and the
+ * near/all tile pairs since the last call.
+ */
+typedef struct steps_ens steps_ens;
+steps_status steps_ensemble_init(steps_ens **out, int nsims, const int64_t *n,
+                                 const double *const *pos, const double *const *vel,
+                                 const double *const *mass, const double *const *soft,
+                                 const double *h_min, const double *t0, const double *a0,
+                                 const steps_config *cfgs, void *cuda_stream);
+steps_status steps_ensemble_run(steps_ens *e, int nsteps, const double *dts);
+steps_status steps_ensemble_get_state(steps_ens *e, int sim, double *pos, double *vel, double *acc,
+                                      double *t, double *a);
+steps_status steps_ensemble_stats(steps_ens *e, int64_t *total_particles, uint64_t *near_pairs,
+                                  uint64_t *all_pairs);
+void steps_ensemble_free(steps_ens *e);
+
+/*
  * Near-field threshold of the FP32 path (default 1/32): a source tile is
  * summed with the compensated near-field method when its bounding box comes
  * closer to the target tile than alpha x (centre distance + both extents);

@@ -33,6 +33,34 @@ steps_status cuda_status(cudaError_t e, const char *what) {
     return e == cudaErrorMemoryAllocation ? STEPS_ENOMEM : STEPS_ECUDA;
 }
 
+steps_status counted_malloc(void **p, size_t bytes) {
+    *p = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        if (g_mem_limit && g_mem_used + bytes > g_mem_limit) {
+            set_error("device allocation of %zu bytes exceeds the library memory limit (%zu of %zu used)",
+                      bytes, g_mem_used, g_mem_limit);
+            return STEPS_ENOMEM;
+        }
+        g_mem_used += bytes;
+    }
+    cudaError_t e = cudaMalloc(p, bytes ? bytes : 16);
+    if (e != cudaSuccess) {
+        std::lock_guard<std::mutex> lk(g_mem_mu);
+        g_mem_used -= bytes;
+        *p = nullptr;
+        return cuda_status(e, "cudaMalloc");
+    }
+    return STEPS_OK;
+}
+
+void counted_free(void *p, size_t bytes) {
+    if (!p) return;
+    cudaFree(p);
+    std::lock_guard<std::mutex> lk(g_mem_mu);
+    g_mem_used -= bytes;
+}
+
 }  // namespace steps
 
 using namespace steps;
@@ -61,6 +89,7 @@ struct steps_ctx {
     Staging stg;
     float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
     NearScratch nr;                       // near-field bitmap and work items
+    SimDesc *dsim = nullptr;              // device table of one system
     unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
     float alpha = 0.03125f;
     int64_t np = 0, ntile_cap = 0;
@@ -172,7 +201,12 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.rdup = c->rdup_buf;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
-    c->plan = plan_force(c->stg, k, c->num_sms);
+    SimDesc d{};
+    d.tile_off = 0;
+    d.ntile = c->stg.ntile;
+    c->plan = plan_force_multi(k, c->num_sms, &d, 1, c->dsim, &c->nr.bits_words);
+    STEPS_CUDA(cudaMemcpyAsync(c->dsim, &d, sizeof(d), cudaMemcpyHostToDevice, c->st));
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
     c->nr.cap_items = 8 * (c->np / c->stg.T);
     if (c->plan.partial_elems > c->partial_cap) {
         dev_free(c, c->partial);
@@ -360,6 +394,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->nr.cnt, c->ntile_cap));
     STEPS_TRY(alloc_n(c, &c->nr.item_off, c->ntile_cap + 1));
     STEPS_TRY(alloc_n(c, &c->nr.meta, 4));
+    STEPS_TRY(alloc_n(c, &c->dsim, 1));
     // near-field work-item partials: up to 8 items per target tile (the chunk
     // size adapts on the device), 3 doubles per particle per item
     STEPS_TRY(alloc_n(c, &c->nr.item_part, (size_t)24 * c->np));

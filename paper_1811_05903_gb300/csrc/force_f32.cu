@@ -35,6 +35,9 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "steps_internal.h"
 
 namespace steps {
@@ -205,13 +208,34 @@ struct ForceArgs {
     int64_t *near_meta;                // {chunk, items, work counter}
     int *err;
     unsigned long long *stats;         // [2]: near tile pairs, all tile pairs (may be null)
-    int64_t ntile;
-    int64_t words;                     // 32-bit words per bitmap row
-    int64_t units;
+    const SimDesc *__restrict__ sims;  // independent systems (one for a single simulation)
+    int nsims;
+    int64_t ntile;                     // tiles, all systems
+    int64_t units;                     // tile pairs, all systems
     int smax;
     float alpha2;                      // near-field criterion, squared
     long long wait_ns;
 };
+
+// System holding stream-K unit u (last table entry whose unit_off <= u).
+__device__ __forceinline__ int sim_of_unit(const SimDesc *__restrict__ sims, int nsims, int64_t u) {
+    int lo = 0, hi = nsims;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sims[mid].unit_off <= u) lo = mid; else hi = mid;
+    }
+    return lo;
+}
+
+// System holding global tile r.
+__device__ __forceinline__ int sim_of_tile(const SimDesc *__restrict__ sims, int nsims, int64_t r) {
+    int lo = 0, hi = nsims;
+    while (hi - lo > 1) {
+        const int mid = (lo + hi) >> 1;
+        if (sims[mid].tile_off <= r) lo = mid; else hi = mid;
+    }
+    return lo;
+}
 
 // Far field of the pair term over this CTA's stream-K range of tile pairs.
 //   KI    targets per thread (KI/2 packed pairs), T = 32 KI particles per tile
@@ -261,25 +285,28 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
 
     if (warp == W) {
         // ---------------- producer warp ----------------
+        // walk (system, target block, source tile) through the unit range
         int64_t k = 0;
         bool ok = true;
-        int64_t cur_blk = -1;
+        int sidx = sim_of_unit(a.sims, a.nsims, u0);
+        SimDesc d = a.sims[sidx];
+        int64_t blk = (u0 - d.unit_off) / d.ntile;
+        int64_t jt = (u0 - d.unit_off) - blk * d.ntile;
+        bool reload = true;
         float4 ci = make_float4(0.f, 0.f, 0.f, 0.f), ei = ci;
         unsigned long long n_near = 0;
         for (; k < count; ++k) {
             const int s = (int)(k % NS);
-            const int64_t u = u0 + k;
-            const int64_t blk = u / a.ntile;
-            const int64_t jt = u - blk * a.ntile;
-            if (blk != cur_blk) {
-                cur_blk = blk;
+            if (reload) {
+                reload = false;
                 if (lane < W) {
-                    ci = a.tbox_c[blk * W + lane];
-                    ei = a.tbox_e[blk * W + lane];
+                    ci = a.tbox_c[d.tile_off + blk * W + lane];
+                    ei = a.tbox_e[d.tile_off + blk * W + lane];
                 }
             }
-            const float4 cj = a.tbox_c[jt];
-            const float4 ej = a.tbox_e[jt];
+            const int64_t gjt = d.tile_off + jt;
+            const float4 cj = a.tbox_c[gjt];
+            const float4 ej = a.tbox_e[gjt];
             bool near = false;
             float dcx = 0.f, dcy = 0.f, dcz = 0.f, edx = 0.f, edy = 0.f, edz = 0.f;
             if (lane < W) {
@@ -288,8 +315,8 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                 dcy = two_diff(ci.y, cj.y, edy);
                 dcz = two_diff(ci.z, cj.z, edz);
                 if (near) {
-                    const int64_t itile = blk * W + lane;
-                    atomicOr(&a.nearbits[itile * a.words + (jt >> 5)], 1u << (jt & 31));
+                    atomicOr(&a.nearbits[d.bits_off + (blk * W + lane) * d.words + (jt >> 5)],
+                             1u << (jt & 31));
                     ++n_near;
                 }
             }
@@ -312,7 +339,16 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                 __threadfence_block();  // the other lanes' metadata before the release-arrive
                 const uint32_t full = smem_u32(&bars[s]);
                 mbar_arrive_expect_tx(full, BYTES_J);
-                bulk_g2s(smem_u32(sj + (size_t)s * 2 * T), a.jdup + jt * 2 * T, BYTES_J, full);
+                bulk_g2s(smem_u32(sj + (size_t)s * 2 * T), a.jdup + gjt * 2 * T, BYTES_J, full);
+            }
+            // next unit
+            if (++jt == d.ntile) {
+                jt = 0;
+                reload = true;
+                if (++blk * W == d.ntile) {
+                    blk = 0;
+                    if (++sidx < a.nsims) d = a.sims[sidx];
+                }
             }
         }
         if (lane == 0) {
@@ -339,10 +375,12 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
     int64_t u = u0;
     int64_t k = 0;
     int seg = 0;
+    int sidx = sim_of_unit(a.sims, a.nsims, u0);
+    SimDesc d = a.sims[sidx];
+    int64_t blk = (u0 - d.unit_off) / d.ntile;
     while (u < u1) {
-        const int64_t blk = u / a.ntile;
-        const int64_t seg_end = min(u1, (blk + 1) * a.ntile);
-        const int64_t ibase = (blk * W + warp) * T + lane * KI;
+        const int64_t seg_end = min(u1, d.unit_off + (blk + 1) * d.ntile);
+        const int64_t ibase = (d.tile_off + blk * W + warp) * T + lane * KI;
         // stash this lane's target offsets in shared memory (read again per tile)
         __syncwarp();
 #pragma unroll
@@ -519,6 +557,10 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
             P[2 * B_I + loc + 2 * q + 1] = (double)hz[q].y + (double)cz_[q].y;
         }
         ++seg;
+        if (++blk * W == d.ntile) {
+            blk = 0;
+            if (++sidx < a.nsims) d = a.sims[sidx];
+        }
     }
 }
 
@@ -575,13 +617,15 @@ __device__ __forceinline__ int64_t select_near(const uint32_t *__restrict__ row,
 }
 
 // Per target tile: number of near source tiles (one warp per row).
-__global__ void near_count_kernel(const uint32_t *__restrict__ bits, int64_t ntile, int64_t words,
-                                  int *__restrict__ cnt) {
+__global__ void near_count_kernel(const uint32_t *__restrict__ bits, const SimDesc *__restrict__ sims,
+                                  int nsims, int64_t ntile, int *__restrict__ cnt) {
     const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (row >= ntile) return;
+    const SimDesc d = sims[sim_of_tile(sims, nsims, row)];
+    const uint32_t *r = bits + d.bits_off + (row - d.tile_off) * d.words;
     int c = 0;
-    for (int64_t w = lane; w < words; w += 32) c += __popc(bits[row * words + w]);
+    for (int64_t w = lane; w < d.words; w += 32) c += __popc(r[w]);
     for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
     if (lane == 0) cnt[row] = c;
 }
@@ -690,7 +734,8 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
         const int64_t itile = lo;
         const int64_t first = (item - a.item_off[itile]) * chunk;
         const int64_t last = min((int64_t)a.near_cnt[itile], first + chunk);
-        const uint32_t *row = a.nearbits + itile * a.words;
+        const SimDesc d = a.sims[sim_of_tile(a.sims, a.nsims, itile)];
+        const uint32_t *row = a.nearbits + d.bits_off + (itile - d.tile_off) * d.words;
 
         const float4 ci = a.tbox_c[itile];
         const float4 ei = a.tbox_e[itile];
@@ -716,12 +761,12 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
             hx[q] = hy[q] = hz[q] = make_float2(0.f, 0.f);
             cx_[q] = cy_[q] = cz_[q] = make_float2(0.f, 0.f);
         }
-        int64_t jt = select_near(row, a.words, first, lane);
+        int64_t jt = select_near(row, d.words, first, lane);
         int b = 0;
-        if (jt >= 0) issue(jt, b);
+        if (jt >= 0) issue(d.tile_off + jt, b);
         for (int64_t rk = first; rk < last && jt >= 0; ++rk) {
-            const int64_t jn = (rk + 1 < last) ? next_near(row, a.words, jt + 1, lane) : -1;
-            if (jn >= 0) issue(jn, b ^ 1);
+            const int64_t jn = (rk + 1 < last) ? next_near(row, d.words, jt + 1, lane) : -1;
+            if (jn >= 0) issue(d.tile_off + jn, b ^ 1);
             bool got = true;
             if (lane == 0) got = mbar_wait_bounded(smem_u32(&bars[b]), (uint32_t)(uses[b] & 1), a.wait_ns);
             if (!__shfl_sync(0xffffffffu, got, 0)) {
@@ -737,7 +782,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
             uses[b] += 1;
             const float4 *S = buf + (size_t)b * 4 * T;  // jdup tile
             const float4 *Rr = S + 2 * T;               // rdup tile
-            const float4 cj = a.tbox_c[jt];
+            const float4 cj = a.tbox_c[d.tile_off + jt];
             float edx, edy, edz;
             const float dcx = two_diff(ci.x, cj.x, edx);
             const float dcy = two_diff(ci.y, cj.y, edy);
@@ -849,28 +894,31 @@ __device__ __forceinline__ int64_t cta_start(int64_t c, int64_t units, int64_t G
     return c * units / G;
 }
 
-// Sum the per-CTA partials of each target in CTA order; apply G; sorted order.
+// Sum the per-CTA far-field partials of each target in CTA order, then its
+// near-field work items in item order; apply G (sorted order, all systems).
 __global__ void fixup_kernel(const double *__restrict__ partial, const double *__restrict__ item_part,
-                             const int64_t *__restrict__ item_off, int T, int64_t n,
-                             int64_t ntile, int64_t units, int64_t G, int smax, int B_I, double Gc,
-                             double *__restrict__ ax, double *__restrict__ ay,
+                             const int64_t *__restrict__ item_off, const SimDesc *__restrict__ sims,
+                             int nsims, int T, int W, int64_t n, int64_t units, int64_t G, int smax,
+                             double Gc, double *__restrict__ ax, double *__restrict__ ay,
                              double *__restrict__ az) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
-    const int64_t blk = p / B_I;
-    const int loc = (int)(p - blk * B_I);
-    const int64_t ufirst = blk * ntile;
-    const int64_t ulast = ufirst + ntile - 1;
+    const int B_I = W * T;
+    const int64_t row = p / T;
+    const SimDesc d = sims[sim_of_tile(sims, nsims, row)];
+    const int64_t blk = (row - d.tile_off) / W;
+    const int loc = (int)(p - (d.tile_off + blk * W) * T);
+    const int64_t ufirst = d.unit_off + blk * d.ntile;
+    const int64_t ulast = ufirst + d.ntile - 1;
+    const int64_t gblk = d.blk_off + blk;
     auto cta_of = [&](int64_t uu) {
         int64_t c = uu * G / units;
         while (c + 1 < G && cta_start(c + 1, units, G) <= uu) ++c;
         while (c > 0 && cta_start(c, units, G) > uu) --c;
         return c;
     };
-    const int64_t clo = cta_of(ufirst), chi = cta_of(ulast);
     double sx = 0.0, sy = 0.0, sz = 0.0;
     {
-        const int64_t row = p / T;
         const int li = (int)(p - row * T);
         for (int64_t it = item_off[row]; it < item_off[row + 1]; ++it) {
             const double *Q = item_part + (size_t)it * 3 * T;
@@ -879,8 +927,11 @@ __global__ void fixup_kernel(const double *__restrict__ partial, const double *_
             sz += Q[2 * T + li];
         }
     }
+    const int64_t clo = cta_of(ufirst), chi = cta_of(ulast);
     for (int64_t c = clo; c <= chi; ++c) {
-        const int64_t seg = blk - cta_start(c, units, G) / ntile;
+        const int64_t us = cta_start(c, units, G);
+        const SimDesc dc = sims[sim_of_unit(sims, nsims, us)];
+        const int64_t seg = gblk - (dc.blk_off + (us - dc.unit_off) / dc.ntile);
         const double *P = partial + ((size_t)(c * smax + seg) * 3) * B_I;
         sx += P[loc];
         sy += P[B_I + loc];
@@ -933,13 +984,31 @@ int num_variants() { return kNumVariants; }
 const Variant &variant(int k) { return kVariants[k].v; }
 size_t force_smem_bytes(int k) { return kVariants[k].smem; }
 
-ForcePlan plan_force(const Staging &s, int k, int num_sms) {
+ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const SimDesc *dev_sims,
+                           int64_t *bits_words) {
     const VariantImpl &vi = kVariants[k];
+    const int W = vi.v.W;
     ForcePlan p;
     p.variant = k;
-    p.B_I = vi.v.W * 32 * vi.v.KI;
-    p.niblk = s.np / p.B_I;
-    p.units = p.niblk * s.ntile;
+    p.B_I = W * 32 * vi.v.KI;
+    p.sims = dev_sims;
+    p.nsims = nsims;
+    int64_t units = 0, blocks = 0, bits = 0;
+    std::vector<int64_t> starts;  // unit at which every target block starts
+    for (int s = 0; s < nsims; ++s) {
+        SimDesc &d = descs[s];
+        d.unit_off = units;
+        d.blk_off = blocks;
+        d.words = (d.ntile + 31) / 32;
+        d.bits_off = bits;
+        for (int64_t b = 0; b < d.ntile / W; ++b) starts.push_back(units + b * d.ntile);
+        units += (d.ntile / W) * d.ntile;
+        blocks += d.ntile / W;
+        bits += d.ntile * d.words;
+    }
+    if (bits_words) *bits_words = bits;
+    p.niblk = blocks;
+    p.units = units;
     int per_sm = 1;
     cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.smem);
     cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
@@ -951,10 +1020,25 @@ ForcePlan plan_force(const Staging &s, int k, int num_sms) {
     if (grid > p.units) grid = p.units;
     if (grid < 1) grid = 1;
     p.grid = (int)grid;
-    const int64_t per_cta = (p.units + grid - 1) / grid;
-    p.smax = (int)((per_cta + s.ntile - 1) / s.ntile + 1);
+    // segments per CTA = target blocks its unit range touches
+    int smax = 1;
+    for (int64_t c = 0; c < grid; ++c) {
+        const int64_t a0 = c * units / grid, a1 = (c + 1) * units / grid;
+        const auto lo = std::upper_bound(starts.begin(), starts.end(), a0);
+        const auto hi = std::lower_bound(starts.begin(), starts.end(), a1);
+        const int segs = 1 + (int)std::max<int64_t>(0, hi - lo);
+        smax = std::max(smax, segs);
+    }
+    p.smax = smax;
     p.partial_elems = (size_t)p.grid * p.smax * 3 * p.B_I;
     return p;
+}
+
+ForcePlan plan_force(const Staging &s, int k, int num_sms) {
+    SimDesc d{};
+    d.tile_off = 0;
+    d.ntile = s.ntile;
+    return plan_force_multi(k, num_sms, &d, 1, nullptr, nullptr);
 }
 
 cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
@@ -972,7 +1056,8 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.near_cnt = nr.cnt;
     a.item_off = nr.item_off;
     a.near_meta = nr.meta;
-    a.words = (s.ntile + 31) / 32;
+    a.sims = p.sims;
+    a.nsims = p.nsims;
     a.err = err;
     a.stats = stats;
     a.ntile = s.ntile;
@@ -980,10 +1065,11 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.smax = p.smax;
     a.alpha2 = alpha * alpha;
     a.wait_ns = wait_ns;
-    cudaError_t e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)s.ntile * a.words, st);
+    cudaError_t e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)nr.bits_words, st);
     if (e != cudaSuccess) return e;
     vi.fn<<<p.grid, (vi.v.W + 1) * 32, vi.smem, st>>>(a);
-    near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, s.ntile, a.words, nr.cnt);
+    near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, p.sims, p.nsims,
+                                                                             s.ntile, nr.cnt);
     near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, nr.item_off, nr.meta);
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vi.near_fn, 32 * kNearWarps, vi.near_smem) !=
@@ -998,8 +1084,9 @@ cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *par
                          cudaStream_t st) {
     const int tb = 256;
     const int64_t blocks = (s.n + tb - 1) / tb;
-    fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(partial, nr.item_part, nr.item_off, s.T, s.n, s.ntile, p.units, p.grid, p.smax,
-                                                  p.B_I, G, ax, ay, az);
+    fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(partial, nr.item_part, nr.item_off, p.sims, p.nsims, s.T,
+                                                  kVariants[p.variant].v.W, s.n, p.units, p.grid, p.smax,
+                                                  G, ax, ay, az);
     return cudaGetLastError();
 }
 

@@ -42,7 +42,7 @@ constexpr size_t align256(size_t x) { return (x + 255) / 256 * 256; }
 
 struct Layout {
     size_t soa, acc, perm, jdup, rdup, tbox_c, tbox_e, partial, bits, cnt, item_off, meta, item_part,
-        err, stats, mmin, total;
+        err, stats, mmin, sim, total;
 };
 
 constexpr Layout make_layout() {
@@ -64,6 +64,7 @@ constexpr Layout make_layout() {
     L.err = o;       o = align256(o + sizeof(int) * 2);
     L.stats = o;     o = align256(o + sizeof(unsigned long long) * 2);
     L.mmin = o;      o = align256(o + sizeof(double));
+    L.sim = o;       o = align256(o + sizeof(SimDesc));
     L.total = o;
     return L;
 }
@@ -189,11 +190,22 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
     s.rdup = reinterpret_cast<float4 *>(base + L.rdup);
     s.tbox_c = reinterpret_cast<float4 *>(base + L.tbox_c);
     s.tbox_e = reinterpret_cast<float4 *>(base + L.tbox_e);
+    SimDesc sd{};
+    sd.tile_off = 0;
+    sd.ntile = s.ntile;
+    sd.unit_off = 0;
+    sd.blk_off = 0;
+    sd.bits_off = 0;
+    sd.words = (s.ntile + 31) / 32;
+    SimDesc *dsim = reinterpret_cast<SimDesc *>(base + L.sim);
+    STEPS_CUDA(cudaMemcpyAsync(dsim, &sd, sizeof(sd), cudaMemcpyHostToDevice, st));
     ForcePlan p;
     p.variant = k;
     p.B_I = (int)kBI;
     p.niblk = s.np / kBI;
     p.units = p.niblk * s.ntile;
+    p.sims = dsim;
+    p.nsims = 1;
     int64_t grid = std::min<int64_t>(p.units, (int64_t)num_sms * 4);
     for (;;) {
         const int64_t per_cta = (p.units + grid - 1) / grid;
@@ -213,6 +225,7 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
     nr.meta = reinterpret_cast<int64_t *>(base + L.meta);
     nr.item_part = reinterpret_cast<double *>(base + L.item_part);
     nr.cap_items = 8 * (kNp / kT);
+    nr.bits_words = s.ntile * sd.words;
     unsigned long long *stats = reinterpret_cast<unsigned long long *>(base + L.stats);
 
     launch_stage(s, x, y, z, m, h, st);

@@ -50,7 +50,7 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
     const int64_t p = tile * T + threadIdx.x;
-    const bool valid = p < n;
+    const bool valid = p < n && !(h[p] < 0.0);  // negative softening marks padding
     double px = 0, py = 0, pz = 0, pm = 0, ph = 0;
     if (valid) {
         px = x[p];
@@ -238,6 +238,97 @@ void launch_stage(const Staging &s, const double *x, const double *y, const doub
                   const double *m, const double *h, cudaStream_t st) {
     stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup,
                                                     s.tbox_c, s.tbox_e);
+}
+
+namespace {
+
+// Ensemble keys: (system << 57) | 57-bit Morton code of the position inside
+// the system's own bounding box; padding sorts to the end of its system.
+__global__ void ens_bbox_kernel(const int64_t *__restrict__ off, const double *__restrict__ x,
+                                const double *__restrict__ y, const double *__restrict__ z,
+                                const double *__restrict__ h, double *__restrict__ bbox) {
+    __shared__ double sbuf[32];
+    const int s = blockIdx.x;
+    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
+    for (int64_t i = off[s] + threadIdx.x; i < off[s + 1]; i += blockDim.x) {
+        if (h[i] < 0.0) continue;
+        const double v[3] = {x[i], y[i], z[i]};
+        for (int k = 0; k < 3; ++k) {
+            lo[k] = fmin(lo[k], v[k]);
+            hi[k] = fmax(hi[k], v[k]);
+        }
+    }
+    for (int k = 0; k < 3; ++k) {
+        const double a = block_reduce(lo[k], sbuf, MinOp());
+        const double b = block_reduce(hi[k], sbuf, MaxOp());
+        if (threadIdx.x == 0) {
+            bbox[6 * s + k] = a;
+            bbox[6 * s + 3 + k] = b;
+        }
+    }
+}
+
+__global__ void ens_morton_kernel(int64_t np_total, int64_t npow2, const int *__restrict__ sim,
+                                  const double *__restrict__ x, const double *__restrict__ y,
+                                  const double *__restrict__ z, const double *__restrict__ h,
+                                  const double *__restrict__ bbox, unsigned long long *__restrict__ keys,
+                                  unsigned int *__restrict__ vals) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= npow2) return;
+    vals[i] = (unsigned int)i;
+    if (i >= np_total) {
+        keys[i] = ~0ull;
+        return;
+    }
+    const unsigned long long s = (unsigned long long)sim[i];
+    const unsigned long long low = (1ull << 57) - 1;
+    if (h[i] < 0.0) {
+        keys[i] = (s << 57) | low;
+        return;
+    }
+    const double *bb = bbox + 6 * s;
+    const double span = fmax(fmax(bb[3] - bb[0], bb[4] - bb[1]), fmax(bb[5] - bb[2], 1e-300));
+    const double scale = 524287.0 / span;
+    const double v[3] = {x[i], y[i], z[i]};
+    unsigned long long c[3];
+    for (int k = 0; k < 3; ++k) {
+        double q = (v[k] - bb[k]) * scale;
+        q = fmin(fmax(q, 0.0), 524287.0);
+        c[k] = (unsigned long long)q;
+    }
+    const unsigned long long code = (spread21(c[0]) << 2) | (spread21(c[1]) << 1) | spread21(c[2]);
+    keys[i] = (s << 57) | (code & (low - 1));
+}
+
+int bitonic_network(SortScratch &s, cudaStream_t st) {
+    const int64_t np2 = s.npow2;
+    int count = 0;
+    for (int64_t k = 2; k <= np2; k <<= 1) {
+        int64_t j = k >> 1;
+        for (; j > 0; j >>= 1) {
+            if (j < 1024 && np2 >= 2048) {
+                bitonic_shared<<<(unsigned)(np2 / 2048), 1024, 0, st>>>(np2, k, j, s.keys, s.vals);
+                ++count;
+                break;
+            }
+            bitonic_global<<<blocks_for(np2, 256), 256, 0, st>>>(np2, j, k, s.keys, s.vals);
+            ++count;
+        }
+    }
+    return count;
+}
+
+}  // namespace
+
+cudaError_t ensemble_sort(int nsims, const int64_t *off, int64_t np_total, const int *sim,
+                          const double *x, const double *y, const double *z, const double *h,
+                          SortScratch &s, cudaStream_t st, int *launches) {
+    ens_bbox_kernel<<<nsims, 512, 0, st>>>(off, x, y, z, h, s.bbox);
+    ens_morton_kernel<<<blocks_for(s.npow2, 256), 256, 0, st>>>(np_total, s.npow2, sim, x, y, z, h,
+                                                                 s.bbox, s.keys, s.vals);
+    const int c = bitonic_network(s, st);
+    if (launches) *launches = 2 + c;
+    return cudaGetLastError();
 }
 
 cudaError_t morton_sort(int64_t n, const double *x, const double *y, const double *z,

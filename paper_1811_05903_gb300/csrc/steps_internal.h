@@ -13,6 +13,9 @@ namespace steps {
 // ---------------------------------------------------------------------------
 void set_error(const char *fmt, ...);
 steps_status cuda_status(cudaError_t e, const char *what);
+// Device allocation counted against the process-wide steps_set_memory_limit cap.
+steps_status counted_malloc(void **p, size_t bytes);
+void counted_free(void *p, size_t bytes);
 
 #define STEPS_CUDA(call)                                                  \
     do {                                                                  \
@@ -55,7 +58,20 @@ struct Staging {
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
 };
 
+// One independent system inside the concatenated staging arrays.  A single
+// simulation is a table of one; an ensemble concatenates its members, each
+// padded to a whole number of target blocks (W tiles).
+struct SimDesc {
+    int64_t tile_off;  // first global tile of the system
+    int64_t ntile;     // its tiles (a multiple of the block's W)
+    int64_t unit_off;  // its first stream-K unit; units = (ntile / W) * ntile
+    int64_t blk_off;   // its first target block in the global block order
+    int64_t bits_off;  // first word of its near bitmap, [ntile][words]
+    int64_t words;     // bitmap words per row, (ntile + 31) / 32
+};
+
 // Launch the staging kernel: FP64 sorted SoA -> FP32 tile-relative arrays.
+// A particle with a negative softening is padding (ensembles).
 void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
                   const double *m, const double *h, cudaStream_t st);
 
@@ -67,20 +83,27 @@ struct NearScratch {
     int64_t *meta = nullptr;      // [3] {chunk, items, work counter}
     double *item_part = nullptr;  // [cap_items][3][T]
     int64_t cap_items = 0;
+    int64_t bits_words = 0;       // words of `bits` in use (cleared per evaluation)
 };
 
-// Stream-K plan for one FP32 force evaluation.
+// Stream-K plan for one FP32 force evaluation over one or more systems.
 struct ForcePlan {
     int variant = 0;
     int grid = 0;       // persistent CTAs
-    int smax = 0;       // max segments (i-blocks touched) per CTA
-    int64_t niblk = 0;
-    int64_t units = 0;  // niblk * ntile
+    int smax = 0;       // max segments (target blocks touched) per CTA
+    int64_t niblk = 0;  // target blocks, all systems
+    int64_t units = 0;  // tile pairs, all systems
     int B_I = 0;
     size_t partial_elems = 0;  // grid * smax * 3 * B_I doubles
+    const SimDesc *sims = nullptr;  // device table
+    int nsims = 1;
 };
 
 ForcePlan plan_force(const Staging &s, int variant, int num_sms);
+// Plan for several systems: descs is the host copy of the table (its unit_off,
+// blk_off and bits_off are filled in here); dev_sims the device copy to use.
+ForcePlan plan_force_multi(int variant, int num_sms, SimDesc *descs, int nsims,
+                           const SimDesc *dev_sims, int64_t *bits_words);
 size_t force_smem_bytes(int variant);
 // alpha: tile pairs whose boxes are closer than alpha * (|c_I - c_J| + |e_I| + |e_J|)
 // take the compensated near-field path.  stats (may be null) counts near/all tile pairs.
@@ -125,6 +148,12 @@ struct SortScratch {
 // Sorts (key, index) pairs; *launches receives the number of kernels issued.
 cudaError_t morton_sort(int64_t n, const double *x, const double *y, const double *z,
                         SortScratch &s, cudaStream_t st, int *launches);
+// Sort an ensemble by (system, Morton code within the system's own box);
+// off[nsims + 1] are the systems' first indices, sim[p] the system of p, and
+// padding (h < 0) sorts to the end of its system.
+cudaError_t ensemble_sort(int nsims, const int64_t *off, int64_t np_total, const int *sim,
+                          const double *x, const double *y, const double *z, const double *h,
+                          SortScratch &s, cudaStream_t st, int *launches);
 // out[k] = in[vals[k]] for k < n
 cudaError_t gather_f64(int64_t n, const unsigned int *vals, const double *in, double *out,
                        cudaStream_t st);

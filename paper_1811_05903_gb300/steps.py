@@ -28,6 +28,8 @@ HEADER_SYMBOLS = [
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
+    "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
+    "steps_ensemble_free",
 ]
 
 
@@ -91,6 +93,15 @@ def load(build_if_missing: bool = False):
     lib.steps_force_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_get_variant.argtypes = [P, ctypes.POINTER(I)]
     lib.steps_set_near_alpha.argtypes = [P, D]
+    PP = ctypes.POINTER(ctypes.c_void_p)
+    lib.steps_ensemble_init.argtypes = [ctypes.POINTER(P), I, P, PP, PP, PP, PP, P, P, P,
+                                        ctypes.POINTER(steps_config), P]
+    lib.steps_ensemble_run.argtypes = [P, I, P]
+    lib.steps_ensemble_get_state.argtypes = [P, I, P, P, P, P, P]
+    lib.steps_ensemble_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_uint64),
+                                         ctypes.POINTER(ctypes.c_uint64)]
+    lib.steps_ensemble_free.argtypes = [P]
+    lib.steps_ensemble_free.restype = None
     lib.steps_forces_noalloc.argtypes = [I64, P, P, P, D, D, P, P]
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
@@ -100,7 +111,8 @@ def load(build_if_missing: bool = False):
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
                  "steps_profile_read", "steps_force_stats", "steps_get_variant",
-                 "steps_forces_noalloc", "steps_set_near_alpha"]:
+                 "steps_forces_noalloc", "steps_set_near_alpha", "steps_ensemble_init",
+                 "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -277,6 +289,69 @@ def steps_variants():
 def make_config(mode=STEPS_STATIC, prec=STEPS_F32_COMP, G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0,
                 Ok=0.0, resort_every=8, tile_override=0) -> steps_config:
     return steps_config(G, H0, Om, OL, Or, Ok, mode, prec, resort_every, tile_override)
+
+
+class Ensemble:
+    """Owner of one ensemble context (many independent simulations)."""
+
+    def __init__(self, members, cfgs, stream=None):
+        """members: list of workloads.Particles-like objects (pos, vel, mass, h_min, t0, a0)."""
+        lib = load()
+        ns = len(members)
+        self.n = [int(p.mass.shape[0]) for p in members]
+        self._keep = []
+        def arr(xs, shape):
+            out = (ctypes.c_void_p * ns)()
+            for k, x in enumerate(xs):
+                if x is None:
+                    out[k] = None
+                    continue
+                a = _f64(x, shape(k))
+                self._keep.append(a)
+                out[k] = ptr(a)
+            return out
+        pos = arr([p.pos for p in members], lambda k: (self.n[k], 3))
+        vel = arr([p.vel for p in members], lambda k: (self.n[k], 3))
+        mass = arr([p.mass for p in members], lambda k: (self.n[k],))
+        n = np.array(self.n, dtype=np.int64)
+        hmin = np.array([p.h_min for p in members], dtype=np.float64)
+        t0 = np.array([p.t0 for p in members], dtype=np.float64)
+        a0 = np.array([p.a0 for p in members], dtype=np.float64)
+        cfg_arr = (steps_config * ns)(*cfgs)
+        h = ctypes.c_void_p()
+        _check(lib.steps_ensemble_init(ctypes.byref(h), ns, ptr(n), pos, vel, mass, None, ptr(hmin),
+                                       ptr(t0), ptr(a0), cfg_arr, stream))
+        self.ctx = h.value
+        self.nsims = ns
+
+    def run(self, dts):
+        """dts: [nsims][nsteps] step lengths."""
+        dts = np.ascontiguousarray(dts, dtype=np.float64)
+        _check(load().steps_ensemble_run(self.ctx, int(dts.shape[1]), dts.ctypes.data))
+
+    def state(self, s):
+        n = self.n[s]
+        pos, vel, acc = np.empty((n, 3)), np.empty((n, 3)), np.empty((n, 3))
+        t, a = ctypes.c_double(), ctypes.c_double()
+        _check(load().steps_ensemble_get_state(self.ctx, s, ptr(pos), ptr(vel), ptr(acc),
+                                               ctypes.byref(t), ctypes.byref(a)))
+        return pos, vel, acc, t.value, a.value
+
+    def stats(self):
+        tp, nn, na = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
+        _check(load().steps_ensemble_stats(self.ctx, ctypes.byref(tp), ctypes.byref(nn), ctypes.byref(na)))
+        return tp.value, nn.value, na.value
+
+    def close(self):
+        if self.ctx:
+            load().steps_ensemble_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Simulation:
