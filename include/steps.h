@@ -263,6 +263,27 @@ steps_status steps_ensemble_stats(steps_ens *e, int64_t *total_particles, uint64
 void steps_ensemble_free(steps_ens *e);
 
 /*
+ * steps_paircount -- exact pair counts DD of nsets point sets in one launch.
+ * The statistics of the density field are what the simulations are run for
+ * (Sec. 1; opening of Sec. 3); the central sphere's two-point correlation
+ * function xi(r) = DD/RR - 1 (natural estimator, RR analytic for a uniform
+ * ball) is the target of the emulator.  The paper gives no counting
+ * algorithm: this is the exact pair count by definition.  Set s is pos[offsets[s] .. offsets[s+1]) of
+ * pos [N][3] (host or device).  Coordinates are quantised about the set's
+ * centre (centres [nsets][3]) to integers q = llround((x - c) * (1/step));
+ * |x - c| / step must stay below 2^29 (else EINVAL), so that |q_i - q_j|^2
+ * fits in int64.  A pair i < j falls in bin b when
+ * edge2[b] <= |q_i - q_j|^2 < edge2[b+1] (edge2 [nbins+1], squared edges in
+ * units of step^2, non-negative and non-decreasing; nbins <= 64).
+ * dd_out [nsets][nbins] (host or device) receives the counts.  Integer
+ * arithmetic throughout: counts are exact and independent of the order of
+ * the additions.  Allocates scratch for the call; synchronises the stream.
+ */
+steps_status steps_paircount(int nsets, const int64_t *offsets, const double *pos,
+                             const double *centres, double step, int nbins, const int64_t *edge2,
+                             uint64_t *dd_out, void *cuda_stream);
+
+/*
  * Near-field threshold of the FP32 path (default 1/32): a source tile is
  * summed with the compensated near-field method when its bounding box comes
  * closer to the target tile than alpha x (centre distance + both extents);

@@ -168,3 +168,21 @@ def paircount(q, edge2) -> np.ndarray:
     dd = np.zeros(nb, dtype=np.uint64)
     _load().oracle_paircount(q.shape[0], _ptr(q), nb, _ptr(edge2), _ptr(dd))
     return dd
+
+
+def ball_pair_cdf(s, R: float):
+    """Fraction of pairs of independent uniform points in a ball of radius R
+    that lie closer than s: the integral of the pair-distance density
+    p(s) = (3 s^2 / R^3)(1 - 3s/(4R) + s^3/(16 R^3)) on [0, 2R]."""
+    x = np.clip(np.asarray(s, dtype=np.float64) / R, 0.0, 2.0)
+    return x ** 3 - 9.0 / 16.0 * x ** 4 + x ** 6 / 32.0
+
+
+def rr_ball(n: int, R: float, edges) -> np.ndarray:
+    """Expected pair counts RR per bin for n uniform points in a ball."""
+    return 0.5 * n * (n - 1) * np.diff(ball_pair_cdf(edges, R))
+
+
+def xi_natural(dd, n: int, R: float, edges) -> np.ndarray:
+    """Natural estimator xi = DD/RR - 1 of the central sphere's correlation function."""
+    return np.asarray(dd, dtype=np.float64) / rr_ball(n, R, edges) - 1.0

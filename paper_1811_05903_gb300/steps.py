@@ -29,7 +29,7 @@ HEADER_SYMBOLS = [
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
-    "steps_ensemble_free",
+    "steps_ensemble_free", "steps_paircount",
 ]
 
 
@@ -100,6 +100,7 @@ def load(build_if_missing: bool = False):
     lib.steps_ensemble_get_state.argtypes = [P, I, P, P, P, P, P]
     lib.steps_ensemble_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64)]
+    lib.steps_paircount.argtypes = [I, P, P, P, D, I, P, P, P]
     lib.steps_ensemble_free.argtypes = [P]
     lib.steps_ensemble_free.restype = None
     lib.steps_forces_noalloc.argtypes = [I64, P, P, P, D, D, P, P]
@@ -112,7 +113,8 @@ def load(build_if_missing: bool = False):
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
                  "steps_profile_read", "steps_force_stats", "steps_get_variant",
                  "steps_forces_noalloc", "steps_set_near_alpha", "steps_ensemble_init",
-                 "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats"]:
+                 "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
+                 "steps_paircount"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -289,6 +291,19 @@ def steps_variants():
 def make_config(mode=STEPS_STATIC, prec=STEPS_F32_COMP, G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0,
                 Ok=0.0, resort_every=8, tile_override=0) -> steps_config:
     return steps_config(G, H0, Om, OL, Or, Ok, mode, prec, resort_every, tile_override)
+
+
+def steps_paircount(offsets, pos, centres, step, edge2, stream=None):
+    """Exact DD counts of point sets; returns uint64 [nsets][nbins]."""
+    offsets = np.ascontiguousarray(offsets, dtype=np.int64)
+    edge2 = np.ascontiguousarray(edge2, dtype=np.int64)
+    pos = _f64(pos, (-1, 3)) if isinstance(pos, np.ndarray) else pos
+    centres = np.ascontiguousarray(centres, dtype=np.float64).reshape(-1, 3)
+    nsets, nbins = offsets.size - 1, edge2.size - 1
+    dd = np.zeros((nsets, nbins), dtype=np.uint64)
+    _check(load().steps_paircount(nsets, ptr(offsets), ptr(pos), ptr(centres), float(step), nbins,
+                                  ptr(edge2), ptr(dd), stream))
+    return dd
 
 
 class Ensemble:

@@ -122,3 +122,38 @@ def test_paircount_matches_kdtree():
     # an integer d^2 < E  <=>  d <= sqrt(E - 1/2); no integer distance sits on that radius
     cum = np.array([(tree.count_neighbors(tree, math.sqrt(E - 0.5)) - n) // 2 for E in edge2])
     np.testing.assert_array_equal(dd.astype(np.int64), np.diff(cum))
+
+
+def test_ball_pair_cdf_against_sampled_pairs():
+    """RR normalisation P(2R) = 1, P(0) = 0, monotone; and the CDF against the
+    distances of independently sampled uniform pairs (Kolmogorov bound)."""
+    R = 3.0
+    assert oracle.ball_pair_cdf(0.0, R) == 0.0 and oracle.ball_pair_cdf(2 * R, R) == 1.0
+    s = np.linspace(0, 2 * R, 1001)
+    assert np.all(np.diff(oracle.ball_pair_cdf(s, R)) >= 0)
+    rng = np.random.default_rng(12)
+    def ball(k):
+        u = rng.uniform(-1, 1, (3 * k, 3))
+        return u[(u ** 2).sum(1) <= 1][:k] * R
+    m = 400_000
+    d = np.sort(np.linalg.norm(ball(m) - ball(m), axis=1))
+    emp = np.arange(1, m + 1) / m
+    ks = np.max(np.abs(emp - oracle.ball_pair_cdf(d, R)))
+    assert ks < 1.63 / math.sqrt(m) * 1.5, ks  # well inside the 1% Kolmogorov quantile
+
+
+def test_xi_of_poisson_ball_is_zero():
+    """Pair counts of a uniform ball through the oracle: xi = 0 within the noise
+    of a U-statistic (a Poisson term 1/sqrt(RR) plus a term of order 1/sqrt(n)
+    from pairs that share a point)."""
+    rng = np.random.default_rng(13)
+    n, R = 2500, 50.0
+    u = rng.uniform(-1, 1, (3 * n, 3))
+    pts = u[(u ** 2).sum(1) <= 1][:n] * R
+    step = R / 2 ** 20
+    q = np.rint(pts / step).astype(np.int32)
+    edges = np.geomspace(5.0, 90.0, 9)
+    dd = oracle.paircount(q, np.ceil((edges / step) ** 2).astype(np.int64))
+    rr = oracle.rr_ball(n, R, edges)
+    xi = oracle.xi_natural(dd, n, R, edges)
+    assert np.all(np.abs(xi) < 5 / np.sqrt(rr) + 4 / math.sqrt(n)), xi
