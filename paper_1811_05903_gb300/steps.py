@@ -30,6 +30,9 @@ HEADER_SYMBOLS = [
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
     "steps_ensemble_free", "steps_paircount",
+    # steps_emu.h
+    "steps_emu_create", "steps_emu_set_data", "steps_emu_train", "steps_emu_predict",
+    "steps_emu_gradients", "steps_emu_get_params", "steps_emu_free",
 ]
 
 
@@ -104,6 +107,14 @@ def load(build_if_missing: bool = False):
     lib.steps_ensemble_free.argtypes = [P]
     lib.steps_ensemble_free.restype = None
     lib.steps_forces_noalloc.argtypes = [I64, P, P, P, D, D, P, P]
+    lib.steps_emu_create.argtypes = [ctypes.POINTER(P), P, I, P]
+    lib.steps_emu_set_data.argtypes = [P, I64, P, P]
+    lib.steps_emu_train.argtypes = [P, I, P, P, P]
+    lib.steps_emu_predict.argtypes = [P, I64, P, P]
+    lib.steps_emu_gradients.argtypes = [P, P, P, P, P]
+    lib.steps_emu_get_params.argtypes = [P, P, P, P, P]
+    lib.steps_emu_free.argtypes = [P]
+    lib.steps_emu_free.restype = None
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
@@ -114,7 +125,8 @@ def load(build_if_missing: bool = False):
                  "steps_profile_read", "steps_force_stats", "steps_get_variant",
                  "steps_forces_noalloc", "steps_set_near_alpha", "steps_ensemble_init",
                  "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
-                 "steps_paircount"]:
+                 "steps_paircount", "steps_emu_create", "steps_emu_set_data", "steps_emu_train",
+                 "steps_emu_predict", "steps_emu_gradients", "steps_emu_get_params"]:
         getattr(lib, name).restype = I
     _lib = lib
     return lib
@@ -304,6 +316,67 @@ def steps_paircount(offsets, pos, centres, step, edge2, stream=None):
     _check(load().steps_paircount(nsets, ptr(offsets), ptr(pos), ptr(centres), float(step), nbins,
                                   ptr(edge2), ptr(dd), stream))
     return dd
+
+
+STEPS_EMU_IN, STEPS_EMU_WIDTH, STEPS_EMU_NPARAMS = 5, 256, 133377
+
+
+def _f32(a, shape):
+    if isinstance(a, np.ndarray) or not hasattr(a, "data_ptr"):
+        return np.ascontiguousarray(a, dtype=np.float32).reshape(shape)
+    return a  # torch tensor: caller guarantees float32, contiguous
+
+
+class Emulator:
+    """Owner of one emulator context (include/steps_emu.h)."""
+
+    def __init__(self, params, batch=1024, stream=None):
+        params = _f32(params, (STEPS_EMU_NPARAMS,))
+        h = ctypes.c_void_p()
+        _check(load().steps_emu_create(ctypes.byref(h), ptr(params), int(batch), stream))
+        self.ctx, self.batch = h.value, int(batch)
+
+    def set_data(self, x, t):
+        x, t = _f32(x, (-1, STEPS_EMU_IN)), _f32(t, (-1,))
+        _check(load().steps_emu_set_data(self.ctx, int(x.shape[0]), ptr(x), ptr(t)))
+
+    def train(self, rows, lr):
+        """rows [nsteps][batch] int32, lr [nsteps]; returns the per-step losses."""
+        rows = np.ascontiguousarray(rows, dtype=np.int32).reshape(-1, self.batch)
+        lr = np.ascontiguousarray(lr, dtype=np.float32).reshape(-1)
+        losses = np.empty(rows.shape[0], dtype=np.float32)
+        _check(load().steps_emu_train(self.ctx, int(rows.shape[0]), ptr(rows), ptr(lr), ptr(losses)))
+        return losses
+
+    def predict(self, x):
+        x = _f32(x, (-1, STEPS_EMU_IN))
+        y = np.empty(x.shape[0], dtype=np.float32)
+        _check(load().steps_emu_predict(self.ctx, int(x.shape[0]), ptr(x), ptr(y)))
+        return y
+
+    def gradients(self, x, t):
+        x, t = _f32(x, (self.batch, STEPS_EMU_IN)), _f32(t, (self.batch,))
+        g = np.empty(STEPS_EMU_NPARAMS, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(load().steps_emu_gradients(self.ctx, ptr(x), ptr(t), ptr(g), ctypes.byref(loss)))
+        return g, loss.value
+
+    def params(self):
+        p, m, v = (np.empty(STEPS_EMU_NPARAMS, dtype=np.float32) for _ in range(3))
+        n = ctypes.c_int64()
+        _check(load().steps_emu_get_params(self.ctx, ptr(p), ptr(m), ptr(v), ctypes.byref(n)))
+        return p, m, v, n.value
+
+    def close(self):
+        if self.ctx:
+            load().steps_emu_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 class Ensemble:

@@ -75,3 +75,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(libbuild, "LIB", str(tmp_path / "absent.so"))
     with pytest.raises(OSError):
         steps.load()
+
+
+def test_emulator_validation_without_gpu(lib):
+    p = np.zeros(steps.STEPS_EMU_NPARAMS, np.float32)
+    with pytest.raises(steps.StepsError) as e:
+        steps.Emulator(p, batch=100)  # not a multiple of 64: rejected before any CUDA call
+    assert e.value.status == steps.STEPS_EINVAL
+    p[3] = np.inf
+    with pytest.raises(steps.StepsError) as e:
+        steps.Emulator(p, batch=64)
+    assert e.value.status == steps.STEPS_EINVAL
