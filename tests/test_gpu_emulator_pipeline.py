@@ -1,0 +1,41 @@
+"""The emulator pipeline end to end at a small size: batched runs, exact pair
+counts through the library, xi against the oracle's counts and analytic RR,
+training, and a prediction better than the training mean."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1811_05903_gb300 import emulator, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_pipeline_small():
+    th_train = workloads.latin_hypercube(12, 40)
+    th_test = workloads.latin_hypercube(3, 41)
+    kw = dict(n_central=2048, n_shells=16, per_shell=128, ngrid=32)
+    runs_train = emulator.generate_runs(th_train, 40, processes=1, **kw)
+    runs_test = emulator.generate_runs(th_test, 41, processes=1, **kw)
+    cen_train, secs = emulator.simulate(runs_train, 12, batch=8)
+    cen_test, _ = emulator.simulate(runs_test, 12, batch=8)
+    assert len(cen_train) == 12 and cen_train[0].shape == (2048, 3) and secs > 0
+    xi, dd, rr, n_in = emulator.measure_xi(cen_train)
+    # counts of one set against the oracle on the same fixed-point coordinates
+    p = cen_train[5]
+    p = p[np.einsum("ij,ij->i", p, p) < emulator.R_XI ** 2]
+    step = emulator.R_XI / 2 ** emulator.FIXED_POINT_BITS
+    v = p / step
+    q = np.where(v >= 0, np.floor(v + 0.5), np.ceil(v - 0.5)).astype(np.int32)
+    edge2 = np.ceil((emulator.bin_edges() / step) ** 2).astype(np.int64)
+    np.testing.assert_array_equal(dd[5], oracle.paircount(q, edge2))
+    np.testing.assert_allclose(rr[5], oracle.rr_ball(int(n_in[5]), emulator.R_XI, emulator.bin_edges()),
+                               rtol=1e-12)
+    np.testing.assert_allclose(xi[5], oracle.xi_natural(dd[5], int(n_in[5]), emulator.R_XI,
+                                                        emulator.bin_edges()), rtol=1e-12)
+    emu = emulator.XiEmulator(seed=3, batch=64)
+    losses = emu.fit(th_train, xi, n_steps=300, lr=1e-3)
+    assert losses[-10:].mean() < losses[:3].mean()
+    xi_te, dd_te, _, _ = emulator.measure_xi(cen_test)
+    pred = emu.predict(th_test)
+    assert pred.shape == xi_te.shape and np.all(np.isfinite(pred))
+    emu.close()
