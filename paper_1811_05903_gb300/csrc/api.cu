@@ -87,7 +87,7 @@ struct steps_ctx {
     int dts_cap = 0;
     // FP32 staging
     Staging stg;
-    float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
+    float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *fdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
     NearScratch nr;                       // near-field bitmap and work items
     SimDesc *dsim = nullptr;              // device table of one system
     unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
@@ -199,6 +199,7 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.ntile = c->stg.np / c->stg.T;
     c->stg.jdup = c->jdup_buf;
     c->stg.rdup = c->rdup_buf;
+    c->stg.fdup = v.form == 1 ? c->fdup_buf : nullptr;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     SimDesc d{};
@@ -390,6 +391,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     c->ntile_cap = c->np / 64;
     STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->rdup_buf, 2 * c->np));
+    STEPS_TRY(alloc_n(c, &c->fdup_buf, 4 * c->np));
     STEPS_TRY(alloc_n(c, &c->nr.bits, (size_t)c->ntile_cap * ((c->ntile_cap + 31) / 32)));
     STEPS_TRY(alloc_n(c, &c->nr.cnt, c->ntile_cap));
     STEPS_TRY(alloc_n(c, &c->nr.item_off, c->ntile_cap + 1));

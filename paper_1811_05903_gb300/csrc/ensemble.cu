@@ -303,6 +303,7 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
     const int64_t ntile = NP / T;
     STEPS_TRY(ens_alloc(e, &e->stg.jdup, 2 * NP));
     STEPS_TRY(ens_alloc(e, &e->stg.rdup, 2 * NP));
+    if (v.form == 1) STEPS_TRY(ens_alloc(e, &e->stg.fdup, 4 * NP));
     STEPS_TRY(ens_alloc(e, &e->stg.tbox_c, ntile));
     STEPS_TRY(ens_alloc(e, &e->stg.tbox_e, ntile));
     e->stg.n = NP;  // validity comes from h >= 0

@@ -195,9 +195,130 @@ __device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei,
     return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
 }
 
+// Far tile pair by expansion about the source tile's centre (EXP variants).
+// With s = fl(o_i + (c_I - c_J)) the target relative to the source tile's
+// centre, n = -s and k_j = m_j^(-2/3) rounded to FP32,
+//     k_j |o_j - s|^2 = k_j |n|^2 + k_j |o_j|^2 + (2 k_j o_j) . n,
+// a four-step FMA chain on the staged coefficients (k_j, k_j |o_j|^2, 2 k_j o_j).
+// Its reciprocal square root w gives w^3 = m_j / r^3 with no mass product, and
+//     sum_j m_j (o_j - s) / r^3 = sum_j w^3 o_j + n sum_j w^3,
+// so an interaction costs 4 (squared distance) + 2 (w^3) + 4 (the two sums)
+// = 10 FP32 lane operations and one MUFU rsqrt, against 12 for the explicit
+// separation.  The rounding of the chain is relative to (|s| + |o_j|)^2
+// instead of r^2; far pairs are never closer than 1/32 of the tiles' distance
+// plus extents (the near-field criterion), which bounds that growth.  Every
+// FOLD sources the sums are combined (S + n S0) and folded into the Kahan
+// state.  The coherent rounding of s is undone to first order with the
+// source tile's monopole tidal tensor, as in the explicit form.
+template <int KI, int T, int FOLD, int UNR, bool SMK, int W>
+__device__ __forceinline__ void far_tile_expansion(
+    const float4 *__restrict__ S, const float4 m0, const float4 m1, const float4 *myipos, int lane,
+    int tid, float2 *skah, float2 (&hx)[KI / 2], float2 (&hy)[KI / 2], float2 (&hz)[KI / 2],
+    float2 (&cx_)[KI / 2], float2 (&cy_)[KI / 2], float2 (&cz_)[KI / 2]) {
+    constexpr int NPAIR = KI / 2;
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    float2 nx[NPAIR], ny[NPAIR], nz[NPAIR], ss[NPAIR];
+    float2 px[NPAIR], py[NPAIR], pz[NPAIR];  // sum of w^3 o_j (starts at the shift correction)
+    {
+        const float2 dcx2 = make_float2(m0.x, m0.x), dcy2 = make_float2(m0.y, m0.y),
+                     dcz2 = make_float2(m0.z, m0.z);
+        const float2 edx2 = make_float2(m1.x, m1.x), edy2 = make_float2(m1.y, m1.y),
+                     edz2 = make_float2(m1.z, m1.z);
+        const float2 ndx = make_float2(-m0.x, -m0.x), ndy = make_float2(-m0.y, -m0.y),
+                     ndz = make_float2(-m0.z, -m0.z);
+        const float2 M2 = make_float2(m0.w, m0.w);
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const float4 i0 = myipos[lane * KI + 2 * q];
+            const float4 i1 = myipos[lane * KI + 2 * q + 1];
+            const float2 xi = make_float2(i0.x, i1.x), yi = make_float2(i0.y, i1.y),
+                         zi = make_float2(i0.z, i1.z);
+            nx[q] = __ffma2_rn(xi, neg1, ndx);
+            ny[q] = __ffma2_rn(yi, neg1, ndy);
+            nz[q] = __ffma2_rn(zi, neg1, ndz);
+            // rounding error of s (exact: Fast2Sum) plus that of c_I - c_J
+            const float2 lx = __fadd2_rn(__fadd2_rn(xi, __fadd2_rn(nx[q], dcx2)), edx2);
+            const float2 ly = __fadd2_rn(__fadd2_rn(yi, __fadd2_rn(ny[q], dcy2)), edy2);
+            const float2 lz = __fadd2_rn(__fadd2_rn(zi, __fadd2_rn(nz[q], dcz2)), edz2);
+            float2 R2 = __fmul2_rn(nx[q], nx[q]);
+            R2 = __ffma2_rn(ny[q], ny[q], R2);
+            R2 = __ffma2_rn(nz[q], nz[q], R2);
+            ss[q] = R2;
+            const float2 Ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
+            const float2 Ri2 = __fmul2_rn(Ri, Ri);
+            const float2 k1 = __fmul2_rn(__fmul2_rn(M2, Ri), Ri2);
+            float2 proj = __fmul2_rn(nx[q], lx);
+            proj = __ffma2_rn(ny[q], ly, proj);
+            proj = __ffma2_rn(nz[q], lz, proj);
+            const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
+            const float2 nk1 = __fmul2_rn(k1, neg1);
+            px[q] = __ffma2_rn(k2, nx[q], __fmul2_rn(nk1, lx));
+            py[q] = __ffma2_rn(k2, ny[q], __fmul2_rn(nk1, ly));
+            pz[q] = __ffma2_rn(k2, nz[q], __fmul2_rn(nk1, lz));
+        }
+    }
+#pragma unroll 1
+    for (int j0 = 0; j0 < T; j0 += FOLD) {
+        float2 p0[NPAIR];  // sum of w^3
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) p0[q] = make_float2(0.f, 0.f);
+#pragma unroll UNR
+        for (int j = j0; j < j0 + FOLD; ++j) {
+            const float4 A = S[4 * j];
+            const float4 B = S[4 * j + 1];
+            const float4 C = S[4 * j + 2];
+            const float4 D = S[4 * j + 3];
+            const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+            const float2 zj = make_float2(B.x, B.y), kj = make_float2(B.z, B.w);
+            const float2 axj = make_float2(C.x, C.y), ayj = make_float2(C.z, C.w);
+            const float2 azj = make_float2(D.x, D.y), bj = make_float2(D.z, D.w);
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                float2 t = __ffma2_rn(kj, ss[q], bj);
+                t = __ffma2_rn(axj, nx[q], t);
+                t = __ffma2_rn(ayj, ny[q], t);
+                t = __ffma2_rn(azj, nz[q], t);
+                const float2 w = make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y));
+                const float2 sc = __fmul2_rn(__fmul2_rn(w, w), w);
+                px[q] = __ffma2_rn(sc, xj, px[q]);
+                py[q] = __ffma2_rn(sc, yj, py[q]);
+                pz[q] = __ffma2_rn(sc, zj, pz[q]);
+                p0[q] = __fadd2_rn(p0[q], sc);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const float2 qx = __ffma2_rn(nx[q], p0[q], px[q]);
+            const float2 qy = __ffma2_rn(ny[q], p0[q], py[q]);
+            const float2 qz = __ffma2_rn(nz[q], p0[q], pz[q]);
+            if (SMK) {
+                float2 *K = skah + q * 32 * W + tid;
+                constexpr int CS = NPAIR * 32 * W;  // component stride
+                float2 h0 = K[0], h1 = K[CS], h2 = K[2 * CS];
+                float2 c0 = K[3 * CS], c1 = K[4 * CS], c2 = K[5 * CS];
+                kahan2(h0, c0, qx);
+                kahan2(h1, c1, qy);
+                kahan2(h2, c2, qz);
+                K[0] = h0;
+                K[CS] = h1;
+                K[2 * CS] = h2;
+                K[3 * CS] = c0;
+                K[4 * CS] = c1;
+                K[5 * CS] = c2;
+            } else {
+                kahan2(hx[q], cx_[q], qx);
+                kahan2(hy[q], cy_[q], qy);
+                kahan2(hz[q], cz_[q], qz);
+            }
+            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
 struct ForceArgs {
     const float4 *__restrict__ jdup;   // [2 np] (ox, ox, oy, oy), (oz, oz, m, m)
     const float4 *__restrict__ rdup;   // [2 np] (rx, rx, ry, ry), (rz, rz, h, h): offset residual, softening
+    const float4 *__restrict__ fdup;   // [4 np] expansion layout (Staging::fdup), expansion variants only
     const float4 *__restrict__ tbox_c; // [ntile] (cx, cy, cz, hmax)
     const float4 *__restrict__ tbox_e; // [ntile] (ex, ey, ez, tile mass)
     double *__restrict__ partial;      // far field: per-CTA, per-segment partial sums
@@ -249,18 +370,23 @@ __device__ __forceinline__ int sim_of_tile(const SimDesc *__restrict__ sims, int
 // compute warps then only see far tile pairs, all of equal cost.
 //   KSM   keep the Kahan state (touched once per FOLD sources) in shared memory
 //         instead of registers, trading LSU work for occupancy
-template <int KI, int W, int NS, bool COMP, int FOLD, int MINB, int UNR, bool KSM>
+//   EXP   far-field arithmetic by expansion about the source tile centre (see
+//         the far-tile branch below): 10 FP32 lane operations per interaction
+//         instead of 12, from the 64-byte-per-source layout Staging::fdup
+template <int KI, int W, int NS, bool COMP, int FOLD, int MINB, int UNR, bool KSM, bool EXP>
 __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
     constexpr int NPAIR = KI / 2;
     constexpr int B_I = W * T;
-    constexpr uint32_t BYTES_J = T * 32u;
+    constexpr int V = EXP ? 4 : 2;  // float4 per source in shared memory
+    constexpr uint32_t BYTES_J = T * 16u * V;
     constexpr bool SMK = COMP && KSM;
     static_assert(T % FOLD == 0, "fold length must divide the tile");
     static_assert(W <= 32, "one producer lane per compute warp");
+    static_assert(!EXP || COMP, "the expansion form is built for compensated sums");
 
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *sj = reinterpret_cast<float4 *>(smem);                                // [NS][2T]
+    float4 *sj = reinterpret_cast<float4 *>(smem);                                // [NS][V T]
     float4 *smeta = reinterpret_cast<float4 *>(smem + NS * BYTES_J);              // [NS][W][2]
     float4 *sipos = smeta + NS * W * 2;                                           // [W][T]
     float2 *skah = reinterpret_cast<float2 *>(sipos + W * T);                     // [6][NPAIR][32 W] (SMK)
@@ -339,7 +465,8 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                 __threadfence_block();  // the other lanes' metadata before the release-arrive
                 const uint32_t full = smem_u32(&bars[s]);
                 mbar_arrive_expect_tx(full, BYTES_J);
-                bulk_g2s(smem_u32(sj + (size_t)s * 2 * T), a.jdup + gjt * 2 * T, BYTES_J, full);
+                const float4 *src = EXP ? a.fdup + gjt * 4 * T : a.jdup + gjt * 2 * T;
+                bulk_g2s(smem_u32(sj + (size_t)s * V * T), src, BYTES_J, full);
             }
             // next unit
             if (++jt == d.ntile) {
@@ -372,6 +499,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
     // ---------------- compute warps ----------------
     const float2 neg1 = make_float2(-1.0f, -1.0f);
     float4 *myipos = sipos + warp * T;
+    const int tid = warp * 32 + lane;
     int64_t u = u0;
     int64_t k = 0;
     int seg = 0;
@@ -391,7 +519,6 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
         }
         float2 hx[NPAIR], hy[NPAIR], hz[NPAIR];     // running sums
         float2 cx_[NPAIR], cy_[NPAIR], cz_[NPAIR];  // Kahan terms (negated), COMP only
-        const int tid = warp * 32 + lane;
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             hx[q] = hy[q] = hz[q] = make_float2(0.f, 0.f);
@@ -410,7 +537,10 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
             }
             const float4 m0 = smeta[(s * W + warp) * 2];
             const float4 m1 = smeta[(s * W + warp) * 2 + 1];
-            if (m1.w == 0.f) {
+            if (EXP && m1.w == 0.f) {
+                far_tile_expansion<KI, T, FOLD, UNR, SMK, W>(sj + (size_t)s * V * T, m0, m1, myipos, lane, tid,
+                                                              skah, hx, hy, hz, cx_, cy_, cz_);
+            } else if (!EXP && m1.w == 0.f) {
                 // Far tile pair.  xs = fl(o_i + dc) loses xs_lo = (o_i + c_I - c_J) - xs,
                 // and that loss is the same for every j of the tile: left alone it would
                 // act as a coherent shift of the target.  Undo it to first order with
@@ -465,7 +595,7 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) force_f32_kernel(const For
                         }
                     }
                 }
-                const float4 *S = sj + (size_t)s * 2 * T;
+                const float4 *S = sj + (size_t)s * V * T;
 #pragma unroll 1
                 for (int j0 = 0; j0 < T; j0 += FOLD) {
 #pragma unroll UNR
@@ -944,9 +1074,9 @@ __global__ void fixup_kernel(const double *__restrict__ partial, const double *_
 
 using KernelFn = void (*)(const ForceArgs);
 
-template <int KI, int W, int NS, bool SMK>
+template <int KI, int W, int NS, bool SMK, bool EXP>
 constexpr size_t smem_of() {
-    return (size_t)NS * (32 * KI) * 32 + (size_t)NS * W * 32 + (size_t)W * (32 * KI) * 16 +
+    return (size_t)NS * (32 * KI) * (EXP ? 64 : 32) + (size_t)NS * W * 32 + (size_t)W * (32 * KI) * 16 +
            (SMK ? (size_t)6 * (KI / 2) * 32 * W * 8 : 0) + 2 * NS * sizeof(uint64_t);
 }
 
@@ -963,18 +1093,25 @@ struct VariantImpl {
     size_t near_smem;
 };
 
-#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, UNR, KSM, NAME)                          \
-    {{KI, W, NS, COMP, NAME}, force_f32_kernel<KI, W, NS, COMP, FOLD, MINB, UNR, KSM>,       \
-     near_f32_kernel<KI, COMP, kNearFold>, smem_of<KI, W, NS, COMP && KSM>(), near_smem_of<KI>()}
+#define STEPS_VARIANT(KI, W, NS, COMP, FOLD, MINB, UNR, KSM, EXP, NAME)                        \
+    {{KI, W, NS, COMP, NAME, EXP ? 1 : 0},                                                     \
+     force_f32_kernel<KI, W, NS, COMP, FOLD, MINB, UNR, KSM, EXP>, near_f32_kernel<KI, COMP, kNearFold>, \
+     smem_of<KI, W, NS, COMP && KSM, EXP>(), near_smem_of<KI>()}
 
+// Compensated variants first (expansion form, then explicit separation), then
+// the naive-sum comparison variants.  The autotuner times every variant of the
+// requested summation mode; systems whose staging has no expansion layout
+// only use the explicit form.
 const VariantImpl kVariants[] = {
-    STEPS_VARIANT(4, 4, 6, true, 32, 3, 4, false, "comp_ki4_w4_u4"),
-    STEPS_VARIANT(4, 8, 6, true, 32, 2, 2, false, "comp_ki4_w8_u2"),
-    STEPS_VARIANT(6, 8, 6, true, 32, 2, 2, false, "comp_ki6_w8_u2"),
-    STEPS_VARIANT(2, 8, 6, true, 32, 4, 4, false, "comp_ki2_w8_u4"),
-    STEPS_VARIANT(4, 4, 6, false, 32, 3, 4, false, "naive_ki4_w4_u4"),
-    STEPS_VARIANT(4, 8, 6, false, 32, 2, 2, false, "naive_ki4_w8_u2"),
-    STEPS_VARIANT(2, 8, 6, false, 32, 4, 4, false, "naive_ki2_w8_u4"),
+    STEPS_VARIANT(4, 4, 4, true, 32, 3, 8, false, true, "exp_ki4_w4_u8"),
+    STEPS_VARIANT(6, 4, 4, true, 32, 2, 4, false, true, "exp_ki6_w4_u4"),
+    STEPS_VARIANT(4, 4, 4, true, 32, 3, 4, false, false, "comp_ki4_w4_u4"),
+    STEPS_VARIANT(4, 8, 4, true, 32, 2, 2, false, false, "comp_ki4_w8_u2"),
+    STEPS_VARIANT(6, 8, 4, true, 32, 2, 2, false, false, "comp_ki6_w8_u2"),
+    STEPS_VARIANT(2, 8, 4, true, 32, 4, 4, false, false, "comp_ki2_w8_u4"),
+    STEPS_VARIANT(4, 4, 4, false, 32, 3, 4, false, false, "naive_ki4_w4_u4"),
+    STEPS_VARIANT(4, 8, 4, false, 32, 2, 2, false, false, "naive_ki4_w8_u2"),
+    STEPS_VARIANT(2, 8, 4, false, 32, 4, 4, false, false, "naive_ki2_w8_u4"),
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1048,6 +1185,7 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     ForceArgs a;
     a.jdup = s.jdup;
     a.rdup = s.rdup;
+    a.fdup = s.fdup;
     a.tbox_c = s.tbox_c;
     a.tbox_e = s.tbox_e;
     a.partial = partial;

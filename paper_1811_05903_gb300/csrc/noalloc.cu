@@ -107,7 +107,7 @@ bool on_device(const void *p) {
 
 int compensated_small_variant() {
     for (int k = 0; k < num_variants(); ++k)
-        if (variant(k).comp && variant(k).KI == kKI && variant(k).W == kW) return k;
+        if (variant(k).comp && variant(k).form == 0 && variant(k).KI == kKI && variant(k).W == kW) return k;
     return -1;
 }
 

@@ -46,7 +46,8 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              const double *__restrict__ y, const double *__restrict__ z,
                              const double *__restrict__ m, const double *__restrict__ h,
                              float4 *__restrict__ jdup, float4 *__restrict__ rdup,
-                             float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e) {
+                             float4 *__restrict__ fdup, float4 *__restrict__ tbox_c,
+                             float4 *__restrict__ tbox_e) {
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
     const int64_t p = tile * T + threadIdx.x;
@@ -96,6 +97,32 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     jdup[2 * p + 1] = make_float4(oz, oz, fm, fm);
     rdup[2 * p] = make_float4(rx, rx, ry, ry);
     rdup[2 * p + 1] = make_float4(rz, rz, fh, fh);
+    if (fdup) {
+        // Far-field expansion: with k = m^(-2/3) rounded once to FP32,
+        //   k |o_j - s|^2 = k |s|^2 + k |o_j|^2 - 2 k o_j . s
+        // so (k |o_j - s|^2)^(-3/2) = m_j / |o_j - s|^3 (to the rounding of k).
+        // The coefficients are formed in FP64 from the FP32 values actually used.
+        float fk, ax, ay, az, fb;
+        if (valid) {
+            const double cm = cbrt(pm);
+            fk = __double2float_rn(1.0 / (cm * cm));
+            const double k = (double)fk;
+            ax = __double2float_rn(2.0 * k * (double)ox);
+            ay = __double2float_rn(2.0 * k * (double)oy);
+            az = __double2float_rn(2.0 * k * (double)oz);
+            fb = __double2float_rn(
+                k * ((double)ox * (double)ox + (double)oy * (double)oy + (double)oz * (double)oz));
+        } else {
+            // k |o - s|^2 evaluates to +inf for every target: the pair adds exactly 0
+            fk = 1.0e10f;
+            ax = ay = az = 0.f;
+            fb = __int_as_float(0x7f800000);
+        }
+        fdup[4 * p] = make_float4(ox, ox, oy, oy);
+        fdup[4 * p + 1] = make_float4(oz, oz, fk, fk);
+        fdup[4 * p + 2] = make_float4(ax, ax, ay, ay);
+        fdup[4 * p + 3] = make_float4(az, az, fb, fb);
+    }
     if (threadIdx.x == 0) {
         // extents and softening rounded up so the box tests stay conservative
         tbox_c[tile] = make_float4(cx, cy, cz, __double2float_ru(hmax));
@@ -237,7 +264,7 @@ inline unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) /
 void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
                   const double *m, const double *h, cudaStream_t st) {
     stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup,
-                                                    s.tbox_c, s.tbox_e);
+                                                    s.fdup, s.tbox_c, s.tbox_e);
 }
 
 namespace {

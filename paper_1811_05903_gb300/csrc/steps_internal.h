@@ -41,6 +41,11 @@ struct Variant {
     int KI, W, NS;
     bool comp;
     const char *name;
+    // far-field arithmetic: 0 = explicit separation d = o_j - s (12 FP32 lane
+    // operations per interaction), 1 = expansion of |o_j - s|^2 about the
+    // source tile centre with the mass folded into the squared distance
+    // (10 lane operations; reads Staging::fdup)
+    int form;
 };
 
 int num_variants();
@@ -54,6 +59,10 @@ struct Staging {
     int64_t ntile = 0;    // np / T
     float4 *jdup = nullptr;   // [2 np] (ox, ox, oy, oy), (oz, oz, m, m): FP32 offsets from the tile centre
     float4 *rdup = nullptr;   // [2 np] (rx, rx, ry, ry), (rz, rz, h, h): FP32 residual x - c - o, softening
+    // [4 np] far-field expansion layout, or null when no expansion variant runs:
+    // (ox, ox, oy, oy), (oz, oz, k, k), (2k ox, 2k ox, 2k oy, 2k oy), (2k oz, 2k oz, k |o|^2, k |o|^2)
+    // with k = fl(m^(-2/3)); padding: o = 1e15, k = 1e10, 2k o = 0, k |o|^2 = +inf
+    float4 *fdup = nullptr;
     float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
 };

@@ -85,7 +85,7 @@ def test_compactified_all_variants(n_central, per_shell):
     ref = oracle.pair_acc(p.pos, p.mass, h, p.G)
     names = steps.steps_variants()
     for k, name in enumerate(names):
-        prec = steps.STEPS_F32_COMP if name.startswith("comp") else steps.STEPS_F32_NAIVE
+        prec = steps.STEPS_F32_NAIVE if name.startswith("naive") else steps.STEPS_F32_COMP
         e = rel_err(gpu_forces(p, prec, tile_override=k + 1, comoving=True), ref)
         rms = np.sqrt(np.mean(e ** 2))
         if prec == steps.STEPS_F32_COMP:

@@ -30,7 +30,12 @@ def test_noalloc_matches_regular_entry_point_twice(n_central, n_shells, per_shel
     steps.load(build_if_missing=True)
     p = workloads.compactified(71, n_central, n_shells, per_shell)
     assert p.n <= steps.STEPS_NOALLOC_MAX_N
-    cfg = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_COMP, Om=p.Om, OL=p.OL)
+    # the regular entry point run with the kernel variant the allocation-free
+    # one uses (64-particle tiles, explicit separations), so that both sides
+    # make the same FP32 roundings up to the order of the partial sums
+    k = steps.steps_variants().index("comp_ki2_w8_u4") + 1
+    cfg = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_COMP, Om=p.Om, OL=p.OL,
+                            tile_override=k)
     sim = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg)
     ref = sim.forces()
     sim.close()
