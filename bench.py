@@ -34,6 +34,11 @@ METRIC = "pair interactions/s at N=2^20: mixed vs FP64 GPU at <=1e-6 rms rel for
 UNIT = "interactions/s"
 FLOP_PER_INTERACTION = 20  # the usual direct N-body convention
 L2_FLUSH_BYTES = 512 << 20
+# DRAM bytes (read + write) of one far-field launch, from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) of the first launch of
+# the named variant on the N = 2^20 workload; reported only for that variant
+# and size (profiles/force_far_expansion_1m.md).
+FAR_TRAFFIC_BYTES = {("exp_ki4_w4_u8", 1048576): 5164149504 + 45248512}
 
 
 def peaks():
@@ -285,6 +290,7 @@ def run_ours(args):
         sim.step(dts[k])
     torch.cuda.synchronize()
     steps.steps_profile_read(sim.ctx, reset=True)
+    steps.steps_force_stats(sim.ctx)  # restart the near/far tile-pair counts
     steps.steps_profile_enable(sim.ctx, True)
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -305,6 +311,7 @@ def run_ours(args):
     if ws > 1:
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    far_ms, far_launches = steps.steps_profile_read_far(sim.ctx)
     force_ms, force_launches, kernel_launches = steps.steps_profile_read(sim.ctx, reset=True)
     near_pairs, all_pairs = steps.steps_force_stats(sim.ctx)
     steps.steps_profile_enable(sim.ctx, False)
@@ -342,7 +349,13 @@ def run_ours(args):
         return
     clocks = clk.summary()
     force_avg_s = force_ms * 1e-3 / max(force_launches, 1)
-    achieved = FLOP_PER_INTERACTION * n * n / force_avg_s / 1e12
+    far_avg_s = far_ms * 1e-3 / max(far_launches, 1)
+    near_frac = near_pairs / max(all_pairs, 1)
+    # the far-field kernel evaluates every tile pair not marked near: all its
+    # targets against all sources of those tiles (N^2 (1 - near fraction) at
+    # equal tile sizes); the near-field kernel does the rest
+    far_interactions = n * n * (1.0 - near_frac)
+    achieved = FLOP_PER_INTERACTION * far_interactions / far_avg_s / 1e12
     pk = peaks()
     max_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
@@ -355,10 +368,13 @@ def run_ours(args):
                    "l2": "flushed between timed steps (%d MiB write)" % (L2_FLUSH_BYTES >> 20),
                    "variant": variant_name},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
-                     "kernel": "force_f32_kernel (pair forces)",
-                     "basis": "%d flop/interaction x N^2 per launch / mean launch time; peak = %d SMs x 128 FP32 lanes x 2 x %.0f MHz"
-                              % (FLOP_PER_INTERACTION, props.multi_processor_count, max_mhz),
+                     "frac": achieved / peak, "traffic": FAR_TRAFFIC_BYTES.get((variant_name, n)),
+                     "kernel": "force_f32_kernel (far field, %s)" % variant_name,
+                     "basis": "%d flop/interaction x N^2 (1 - near tile-pair fraction %.4f) per launch / mean far-field "
+                              "launch time (CUDA events on the launching stream, %d launches); peak = %d SMs x 128 FP32 "
+                              "lanes x 2 x %.0f MHz (FP32 FMA pipe, no measured FP32 peak on file)"
+                              % (FLOP_PER_INTERACTION, near_frac, far_launches, props.multi_processor_count, max_mhz),
+                     "pair_force_evaluation_tflops": FLOP_PER_INTERACTION * n * n / force_avg_s / 1e12,
                      "frac_at_observed_clock": (achieved / fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
                                                 if clocks.get("sm_mhz") else None)},
         "cpu_baseline": cpu,
@@ -373,7 +389,7 @@ def run_ours(args):
                         **err.get("f64_gpu", {})},
             "error_targets": int(tg.size),
         },
-        "near_field_fraction": near_pairs / max(all_pairs, 1),
+        "near_field_fraction": near_frac,
         "ensemble": ensemble,
         "wall_s_timed": wall,
     }

@@ -201,6 +201,12 @@ steps_status steps_set_memory_limit(size_t bytes);
 steps_status steps_profile_enable(steps_ctx *ctx, int on);
 steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force_launches,
                                 int64_t *kernel_launches, int reset);
+/*
+ * The far-field kernel alone (FP32 modes): summed device time (ms) of the
+ * far-field launches recorded since the last steps_profile_read reset, and
+ * their count.  Read it before the reset; it does not reset anything itself.
+ */
+steps_status steps_profile_read_far(steps_ctx *ctx, double *far_ms, int64_t *far_launches);
 
 /*
  * steps_forces_noalloc -- the pair term of Eq. 8 (same definition and FP32

@@ -105,6 +105,7 @@ struct steps_ctx {
     // benchmark hooks
     bool profiling = false;
     std::vector<std::pair<cudaEvent_t, cudaEvent_t>> force_events;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> far_events;  // far-field kernel alone
     int64_t force_launches = 0;
     int64_t kernel_launches = 0;
     int64_t *inv = nullptr;   // inverse permutation scratch (subset forces)
@@ -245,10 +246,14 @@ bool capturing(const steps_ctx *c) {
 // Pair term at the current positions into ax, ay, az (sorted order).
 steps_status compute_forces(steps_ctx *c) {
     const bool prof = c->profiling && !capturing(c);
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr, f0 = nullptr, f1 = nullptr;
     if (prof) {
         STEPS_CUDA(cudaEventCreate(&e0));
         STEPS_CUDA(cudaEventCreate(&e1));
+        if (c->cfg.prec != STEPS_F64) {
+            STEPS_CUDA(cudaEventCreate(&f0));
+            STEPS_CUDA(cudaEventCreate(&f1));
+        }
     }
     if (c->cfg.prec == STEPS_F64) {
         if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
@@ -261,7 +266,7 @@ steps_status compute_forces(steps_ctx *c) {
         STEPS_CUDA(cudaGetLastError());
         if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
         STEPS_CUDA(launch_force_f32(c->plan, c->stg, c->partial, c->nr, c->err, c->stats, c->alpha,
-                                    c->wait_ns, c->num_sms, c->st));
+                                    c->wait_ns, c->num_sms, c->st, f0, f1));
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
         STEPS_CUDA(launch_fixup(c->plan, c->stg, c->partial, c->nr, c->cosmo.G, c->ax, c->ay,
                                 c->az, c->st));
@@ -269,6 +274,7 @@ steps_status compute_forces(steps_ctx *c) {
     }
     c->force_launches += 1;
     if (prof) c->force_events.push_back({e0, e1});
+    if (prof && f0) c->far_events.push_back({f0, f1});
     return STEPS_OK;
 }
 
@@ -865,14 +871,33 @@ steps_status steps_profile_read(steps_ctx *c, double *force_ms, int64_t *force_l
     if (force_launches) *force_launches = (int64_t)c->force_events.size();
     if (kernel_launches) *kernel_launches = c->kernel_launches;
     if (reset) {
-        for (auto &ev : c->force_events) {
-            cudaEventDestroy(ev.first);
-            cudaEventDestroy(ev.second);
+        for (auto *list : {&c->force_events, &c->far_events}) {
+            for (auto &ev : *list) {
+                cudaEventDestroy(ev.first);
+                cudaEventDestroy(ev.second);
+            }
+            list->clear();
         }
-        c->force_events.clear();
         c->force_launches = 0;
         c->kernel_launches = 0;
     }
+    return STEPS_OK;
+}
+
+steps_status steps_profile_read_far(steps_ctx *c, double *far_ms, int64_t *far_launches) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    STEPS_CUDA(cudaStreamSynchronize(c->st));
+    double ms = 0.0;
+    for (auto &ev : c->far_events) {
+        float t = 0.f;
+        STEPS_CUDA(cudaEventElapsedTime(&t, ev.first, ev.second));
+        ms += t;
+    }
+    if (far_ms) *far_ms = ms;
+    if (far_launches) *far_launches = (int64_t)c->far_events.size();
     return STEPS_OK;
 }
 

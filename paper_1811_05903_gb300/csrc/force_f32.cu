@@ -1180,7 +1180,8 @@ ForcePlan plan_force(const Staging &s, int k, int num_sms) {
 
 cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
                              const NearScratch &nr, int *err, unsigned long long *stats,
-                             float alpha, long long wait_ns, int num_sms, cudaStream_t st) {
+                             float alpha, long long wait_ns, int num_sms, cudaStream_t st,
+                             cudaEvent_t far_begin, cudaEvent_t far_end) {
     const VariantImpl &vi = kVariants[p.variant];
     ForceArgs a;
     a.jdup = s.jdup;
@@ -1205,7 +1206,9 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.wait_ns = wait_ns;
     cudaError_t e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)nr.bits_words, st);
     if (e != cudaSuccess) return e;
+    if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
     vi.fn<<<p.grid, (vi.v.W + 1) * 32, vi.smem, st>>>(a);
+    if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
     near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, p.sims, p.nsims,
                                                                              s.ntile, nr.cnt);
     near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, nr.item_off, nr.meta);

@@ -120,9 +120,11 @@ size_t force_smem_bytes(int variant);
 // skipped) and the near-field kernel (near_acc [3][np]).
 // Far field (stream-K over tile pairs; marks near pairs in nr.bits, cleared
 // here) then the near-field work items.  5 kernels + 1 memset.
+// far_begin / far_end (may be null): events recorded on st around the far-field launch.
 cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
                              const NearScratch &nr, int *err, unsigned long long *stats,
-                             float alpha, long long wait_ns, int num_sms, cudaStream_t st);
+                             float alpha, long long wait_ns, int num_sms, cudaStream_t st,
+                             cudaEvent_t far_begin = nullptr, cudaEvent_t far_end = nullptr);
 cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial,
                          const NearScratch &nr, double G, double *ax, double *ay, double *az,
                          cudaStream_t st);

@@ -27,6 +27,7 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
+    "steps_profile_read_far",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
     "steps_ensemble_free", "steps_paircount",
@@ -93,6 +94,7 @@ def load(build_if_missing: bool = False):
     lib.steps_forces_subset.argtypes = [P, I64, P, P]
     lib.steps_profile_enable.argtypes = [P, I]
     lib.steps_profile_read.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64), ctypes.POINTER(I64), I]
+    lib.steps_profile_read_far.argtypes = [P, ctypes.POINTER(D), ctypes.POINTER(I64)]
     lib.steps_force_stats.argtypes = [P, ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_get_variant.argtypes = [P, ctypes.POINTER(I)]
     lib.steps_set_near_alpha.argtypes = [P, D]
@@ -122,7 +124,7 @@ def load(build_if_missing: bool = False):
                  "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
-                 "steps_profile_read", "steps_force_stats", "steps_get_variant",
+                 "steps_profile_read", "steps_profile_read_far", "steps_force_stats", "steps_get_variant",
                  "steps_forces_noalloc", "steps_set_near_alpha", "steps_ensemble_init",
                  "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
                  "steps_paircount", "steps_emu_create", "steps_emu_set_data", "steps_emu_train",
@@ -205,6 +207,13 @@ def steps_profile_read(ctx, reset: bool = True):
     _check(load().steps_profile_read(ctx, ctypes.byref(ms), ctypes.byref(fl), ctypes.byref(kl),
                                      1 if reset else 0))
     return ms.value, fl.value, kl.value
+
+
+def steps_profile_read_far(ctx):
+    """(summed far-field kernel ms, far-field launches) since the last profile reset."""
+    ms, fl = ctypes.c_double(), ctypes.c_int64()
+    _check(load().steps_profile_read_far(ctx, ctypes.byref(ms), ctypes.byref(fl)))
+    return ms.value, fl.value
 
 
 def steps_force_stats(ctx):
