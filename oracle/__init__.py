@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  The plain, slow, obviously-correct definition of
 what the GPU library computes: the spline-softened pair sum (Eq. 3, 4, 8), the
 mass-tied softening (Eq. 7), the kick-drift-kick step (Eq. 9-11) with an RK4
-scale factor (Eq. 1), the pair potential, pair counts and the emulator MLP.
+scale factor (Eq. 1), the adaptive step length (Eq. 12), the pair potential,
+pair counts and the emulator MLP.
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
 
@@ -65,6 +66,8 @@ def _load():
         lib.oracle_rk4_a.argtypes = [D, D, ctypes.POINTER(Cosmo)]
         lib.oracle_kdk_step.argtypes = [I64, P, P, P, P, P, D, P, P, ctypes.POINTER(Cosmo)]
         lib.oracle_kinetic.argtypes = [I64, P, P, P, P]
+        lib.oracle_timestep.restype = D
+        lib.oracle_timestep.argtypes = [I64, P, P, P, P, D, D, D, D, ctypes.POINTER(Cosmo)]
         lib.oracle_paircount.argtypes = [I64, P, ctypes.c_int, P, P]
         _lib = lib
     return _lib
@@ -129,6 +132,16 @@ def rk4_a(a: float, dt: float, c: Cosmo) -> float:
     return _load().oracle_rk4_a(float(a), float(dt), ctypes.byref(c))
 
 
+def timestep(pos, vel, acc, h, eps: float, dt_max: float, a: float, c: Cosmo,
+             t_left: float = float("inf")) -> float:
+    """Eq. 12: min(dt_max, min_i sqrt(2 * 2.8 h_i * eps / |A_i|)), A_i the kick's
+    acceleration at the current state (acc = pair term, G included)."""
+    pos, vel, acc = _f64(pos, (-1, 3)), _f64(vel, (-1, 3)), _f64(acc, (-1, 3))
+    h = _f64(h)
+    return _load().oracle_timestep(h.size, _ptr(pos), _ptr(vel), _ptr(acc), _ptr(h), float(eps),
+                                   float(dt_max), float(t_left), float(a), ctypes.byref(c))
+
+
 def kinetic(vel, m):
     vel, m = _f64(vel, (-1, 3)), _f64(m)
     e = ctypes.c_double()
@@ -154,6 +167,17 @@ class KDK:
         _load().oracle_kdk_step(self.m.size, _ptr(self.pos), _ptr(self.vel), _ptr(self.acc),
                                 _ptr(self.m), _ptr(self.h), float(dt), ctypes.byref(self.a),
                                 ctypes.byref(self.t), ctypes.byref(self.c))
+
+    def timestep(self, eps: float, dt_max: float, t_end: float = float("inf")) -> float:
+        """Eq. 12 at the current state, limited to t_end - t."""
+        return timestep(self.pos, self.vel, self.acc, self.h, eps, dt_max, self.a.value, self.c,
+                        t_left=t_end - self.t.value)
+
+    def adaptive_step(self, eps: float, dt_max: float, t_end: float = float("inf")) -> float:
+        """One KDK step (Eq. 9-11) whose length is Eq. 12 at the step's start."""
+        dt = self.timestep(eps, dt_max, t_end)
+        self.step(dt)
+        return dt
 
     def energy(self):
         ek, _ = kinetic(self.vel, self.m)

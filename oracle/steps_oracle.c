@@ -24,6 +24,9 @@
  *   oracle_rk4_a         -- flat LambdaCDM closed form t(a)
  *   oracle_kdk_step      -- Kepler orbit (period, second order), energy
  *                           conservation, uniform comoving sphere at rest
+ *   oracle_timestep      -- closed forms: a bound pair, a lone particle at
+ *                           rest off-centre (background term) and a moving
+ *                           one (friction term); dt_max and t_end limits
  *   oracle_paircount     -- independent k-d tree counts
  *   oracle_mlp_*         -- finite-difference gradients
  */
@@ -211,6 +214,49 @@ void oracle_kdk_step(int64_t n, double *pos, double *vel, double *acc, const dou
     *t += dt;
     oracle_pair_acc(n, pos, m, h, c->G, n, NULL, acc);        /* force   */
     kick(n, vel, pos, acc, 0.5 * dt, *a, c);                  /* K(dt/2) */
+}
+
+/* ------------------------------------------------------------------ */
+/* Eq. 12: adaptive time step of the KDK integrator,                     */
+/*   dt = min(dt_max, min_i sqrt(2 eta_i eps / |A_i|)),                  */
+/* eta_i = 2.8 h_i as printed (the paper calls it the Plummer-equivalent */
+/* softening length), eps the accuracy parameter, and A_i the            */
+/* acceleration the next kick would apply at the current state: the      */
+/* comoving Eq. 8 (pair term / a^3 - 2 H v + background) or, in static    */
+/* mode, the pair term.  A particle with A_i = 0 sets no limit.  If       */
+/* t_left is finite the step is also limited to t_left (never below 0).  */
+/* acc holds the pair term at pos (G included), as for the kick.         */
+/* ------------------------------------------------------------------ */
+double oracle_timestep(int64_t n, const double *pos, const double *vel, const double *acc,
+                       const double *h, double eps, double dt_max, double t_left, double a,
+                       const oracle_cosmo *c)
+{
+    double q_min = INFINITY;
+    double H = 0.0, bg = 0.0, a3 = 1.0;
+    if (c->comoving) {
+        double rho_crit = 3.0 * c->H0 * c->H0 / (8.0 * M_PI * c->G);
+        H = oracle_hubble(a, c);
+        bg = 4.0 * M_PI * c->G / 3.0 * c->Om * rho_crit;
+        a3 = a * a * a;
+    }
+    for (int64_t i = 0; i < n; i++) {
+        double A2 = 0.0;
+        for (int k = 0; k < 3; k++) {
+            double A = acc[3 * i + k];
+            if (c->comoving) A = acc[3 * i + k] / a3 - 2.0 * H * vel[3 * i + k] + bg * pos[3 * i + k] / a3;
+            A2 += A * A;
+        }
+        double Amag = sqrt(A2);
+        if (Amag > 0.0) {
+            double eta = 2.8 * h[i];
+            double q = 2.0 * eta * eps / Amag;
+            if (q < q_min) q_min = q;
+        }
+    }
+    double dt = dt_max;
+    if (q_min < INFINITY && sqrt(q_min) < dt) dt = sqrt(q_min);
+    if (isfinite(t_left) && t_left < dt) dt = t_left > 0.0 ? t_left : 0.0;
+    return dt;
 }
 
 /* Kinetic energy and momentum, 1/2 sum m v^2 and sum m v. */

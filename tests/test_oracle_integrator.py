@@ -157,3 +157,71 @@ def test_xi_of_poisson_ball_is_zero():
     rr = oracle.rr_ball(n, R, edges)
     xi = oracle.xi_natural(dd, n, R, edges)
     assert np.all(np.abs(xi) < 5 / np.sqrt(rr) + 4 / math.sqrt(n)), xi
+
+
+# ---------------------------------------------------------------- Eq. 12 ----
+
+def test_timestep_bound_pair_closed_form():
+    """Two bodies far outside their softening: |A_1| = G m_2 / r^2, |A_2| = G m_1 / r^2,
+    so dt = min_i sqrt(2 * 2.8 h_i * eps * r^2 / (G m_other))."""
+    G, r, eps = 1.7, 3.0, 0.02
+    pos = np.array([[0.0, 0.0, 0.0], [0.0, r, 0.0]])
+    m = np.array([2.0, 0.5])
+    h = np.array([1e-3, 4e-3])
+    acc = oracle.pair_acc(pos, m, h, G)
+    c = oracle.cosmo(G=G, comoving=False)
+    dt = oracle.timestep(pos, np.zeros_like(pos), acc, h, eps, 1e9, 1.0, c)
+    want = min(math.sqrt(2 * 2.8 * h[0] * eps * r * r / (G * m[1])),
+               math.sqrt(2 * 2.8 * h[1] * eps * r * r / (G * m[0])))
+    assert dt == pytest.approx(want, rel=1e-13)
+    # dt_max wins when smaller; a finite time left wins when smaller still; never below 0
+    assert oracle.timestep(pos, np.zeros_like(pos), acc, h, eps, 0.5 * want, 1.0, c) == 0.5 * want
+    assert oracle.timestep(pos, np.zeros_like(pos), acc, h, eps, 1e9, 1.0, c, t_left=0.25 * want) == 0.25 * want
+    assert oracle.timestep(pos, np.zeros_like(pos), acc, h, eps, 1e9, 1.0, c, t_left=-1.0) == 0.0
+
+
+def test_timestep_comoving_background_and_friction_terms():
+    """A lone particle (no pair term) in comoving mode: at rest off-centre it feels
+    only the background term (1/2) Om H0^2 x / a^3; moving through the centre only
+    the friction -2 H(a) v.  Both give dt in closed form; at rest at the centre
+    nothing limits the step and dt = dt_max."""
+    c = oracle.cosmo(G=1.0, H0=1.0, Om=0.3, OL=0.7, comoving=True)
+    a, eps, hh = 0.25, 0.01, np.array([0.05])
+    x = np.array([[3.0, -4.0, 0.0]])
+    zero = np.zeros((1, 3))
+    dt = oracle.timestep(x, zero, zero, hh, eps, 1e9, a, c)
+    A = 0.5 * 0.3 * 5.0 / a ** 3
+    assert dt == pytest.approx(math.sqrt(2 * 2.8 * 0.05 * eps / A), rel=1e-13)
+    v = np.array([[0.0, 0.0, 2.0]])
+    H = math.sqrt(0.3 / a ** 3 + 0.7)
+    dt = oracle.timestep(zero, v, zero, hh, eps, 1e9, a, c)
+    assert dt == pytest.approx(math.sqrt(2 * 2.8 * 0.05 * eps / (2 * H * 2.0)), rel=1e-13)
+    assert oracle.timestep(zero, zero, zero, hh, eps, 0.125, a, c) == 0.125
+
+
+def test_adaptive_kepler_energy_error_scales_with_eps():
+    """Eq. 12 makes dt proportional to sqrt(eps); KDK's energy error goes as dt^2,
+    so on an eccentric orbit it must fall about 4x when eps falls 4x."""
+    def run(eps):
+        e = 0.6
+        ra = 1.0 + e
+        vrel = math.sqrt((1.0 - e) / (1.0 + e))
+        pos = np.array([[0.5 * ra, 0, 0], [-0.5 * ra, 0, 0]])
+        vel = np.array([[0, 0.5 * vrel, 0], [0, -0.5 * vrel, 0]])
+        m = np.array([0.5, 0.5])
+        h = np.array([1e-3, 1e-3])
+        kd = oracle.KDK(pos, vel, m, h, oracle.cosmo(comoving=False))
+        e0 = kd.energy()
+        t_end = 4 * math.pi
+        de, steps = 0.0, 0
+        while kd.t.value < t_end:
+            dt = kd.adaptive_step(eps, 0.05, t_end)
+            steps += 1
+            de = max(de, abs(kd.energy() - e0) / abs(e0))
+            assert dt > 0
+        assert kd.t.value == pytest.approx(t_end, abs=1e-12)
+        return de, steps
+    de1, n1 = run(0.04)
+    de2, n2 = run(0.01)
+    assert 1.7 < n2 / n1 < 2.3          # sqrt(4) more steps
+    assert 3.0 < de1 / de2 < 5.0, (de1, de2)
