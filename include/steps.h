@@ -121,6 +121,35 @@ steps_status steps_kdk_step(steps_ctx *ctx, double dt, double *a_out);
 steps_status steps_kdk_run(steps_ctx *ctx, int nsteps, const double *dts);
 
 /*
+ * Eq. 12 (Sec. 2.3): adaptive step length of the KDK integrator,
+ *   dt = min(dt_max, min_i sqrt(2 eta_i eps / |A_i|)),   eta_i = 2.8 h_i,
+ * with eps the accuracy parameter and A_i the acceleration the next kick
+ * applies at the current state (comoving mode: the pair term / a^3 - 2 H v +
+ * the background term of Eq. 8; static mode: the pair term).  A particle with
+ * A_i = 0 sets no limit.  When t_end is finite the step is also limited to
+ * t_end - t (never below 0); pass +INFINITY for no limit.  eta_i = 2.8 h_i is
+ * taken as printed (the paper calls it the Plummer-equivalent softening; the
+ * spline's own Plummer equivalent is h_i / 2.8, which is the same criterion
+ * with eps divided by 7.84).
+ * steps_timestep computes dt on the device from the forces of the last
+ * evaluation, makes it the length of the next device-resident step and, if
+ * dt_out is not NULL, synchronises and returns it (the caller then passes it
+ * to steps_kdk_step).  EINVAL unless eps and dt_max are finite and > 0 and
+ * t_end is not NaN.
+ */
+steps_status steps_timestep(steps_ctx *ctx, double eps, double dt_max, double t_end, double *dt_out);
+
+/*
+ * nsteps KDK steps (Eq. 11), each of the length Eq. 12 gives at its start,
+ * computed and applied on the device (non-sorting steps replay one CUDA
+ * graph; no host synchronisation between steps).  Steps taken after t has
+ * reached t_end have length 0 and move nothing.  *t_out (may be NULL)
+ * receives the final t.  Same argument checks as steps_timestep.
+ */
+steps_status steps_kdk_run_adaptive(steps_ctx *ctx, int nsteps, double eps, double dt_max, double t_end,
+                                    double *t_out);
+
+/*
  * steps_get_state -- copy the FP64 state out in caller order.  Any pointer
  * may be NULL to skip it.  pos/vel/acc are [n][3]; acc is the pair term at the
  * current positions.  Synchronises the stream.
@@ -240,7 +269,7 @@ steps_status steps_forces_noalloc(int64_t n, const double *pos, const double *ma
 /*
  * Ensembles: many independent simulations of uneven N and differing
  * cosmologies advanced together (batched runs for parameter studies, the use
- * the paper names for fast low-resolution simulations).  Each member is
+ * the paper names for fast low-resolution simulations in its abstract).  Each member is
  * a system of its own -- its particles interact only with each other -- with
  * its own steps_config (G, H0, Om, OL, Or, Ok, mode; precision, re-sort period
  * and tile_override are taken from cfgs[0]), t0, a0 and softening (soft[s], or

@@ -642,6 +642,93 @@ steps_status steps_kdk_run(steps_ctx *c, int nsteps, const double *dts) {
     return sync_and_check(c);
 }
 
+namespace {
+
+steps_status check_timestep_args(const steps_ctx *c, double eps, double dt_max, double t_end) {
+    if (!c) {
+        set_error("ctx is NULL");
+        return STEPS_EINVAL;
+    }
+    if (!(eps > 0.0) || !std::isfinite(eps) || !(dt_max > 0.0) || !std::isfinite(dt_max) ||
+        std::isnan(t_end)) {
+        set_error("eps and dt_max must be finite and > 0, t_end a number (+inf: no limit)");
+        return STEPS_EINVAL;
+    }
+    return STEPS_OK;
+}
+
+cudaError_t issue_timestep(steps_ctx *c, double eps, double dt_max, double t_end) {
+    c->kernel_launches += 2;
+    return launch_timestep(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->ax, c->ay, c->az, c->h, c->sc,
+                           c->cosmo, eps, dt_max, t_end, c->red, c->nred, c->st);
+}
+
+}  // namespace
+
+steps_status steps_timestep(steps_ctx *c, double eps, double dt_max, double t_end, double *dt_out) {
+    STEPS_TRY(check_timestep_args(c, eps, dt_max, t_end));
+    STEPS_CUDA(issue_timestep(c, eps, dt_max, t_end));
+    if (dt_out) {
+        STEPS_CUDA(cudaMemcpyAsync(dt_out, c->sc + SC_DT, sizeof(double), cudaMemcpyDefault, c->st));
+        return sync_and_check(c);
+    }
+    return STEPS_OK;
+}
+
+steps_status steps_kdk_run_adaptive(steps_ctx *c, int nsteps, double eps, double dt_max, double t_end,
+                                    double *t_out) {
+    STEPS_TRY(check_timestep_args(c, eps, dt_max, t_end));
+    if (nsteps < 0) {
+        set_error("nsteps must be >= 0");
+        return STEPS_EINVAL;
+    }
+    // Each step: Eq. 12 on the device at the step's start, then Eq. 11 with
+    // that length.  Steps without a re-sort replay one captured graph.
+    cudaGraphExec_t plain = nullptr;
+    steps_status s = STEPS_OK;
+    for (int k = 0; k < nsteps && s == STEPS_OK; ++k) {
+        const bool do_sort = ++c->since_sort >= resort_every(c);
+        if (do_sort) {
+            if (plain) {
+                cudaGraphExecDestroy(plain);
+                plain = nullptr;
+            }
+            if (issue_timestep(c, eps, dt_max, t_end) != cudaSuccess) s = STEPS_ECUDA;
+            if (s == STEPS_OK) s = issue_step(c, true);
+            continue;
+        }
+        if (!plain) {
+            cudaGraph_t g = nullptr;
+            cudaError_t e = cudaStreamBeginCapture(c->st, cudaStreamCaptureModeThreadLocal);
+            if (e != cudaSuccess) {
+                s = cuda_status(e, "cudaStreamBeginCapture");
+                break;
+            }
+            steps_status si = issue_timestep(c, eps, dt_max, t_end) == cudaSuccess ? STEPS_OK : STEPS_ECUDA;
+            if (si == STEPS_OK) si = issue_step(c, false);
+            e = cudaStreamEndCapture(c->st, &g);
+            if (si != STEPS_OK || e != cudaSuccess) {
+                if (g) cudaGraphDestroy(g);
+                s = si != STEPS_OK ? si : cuda_status(e, "cudaStreamEndCapture");
+                break;
+            }
+            e = cudaGraphInstantiate(&plain, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) {
+                plain = nullptr;
+                s = cuda_status(e, "cudaGraphInstantiate");
+                break;
+            }
+        }
+        cudaError_t e = cudaGraphLaunch(plain, c->st);
+        if (e != cudaSuccess) s = cuda_status(e, "cudaGraphLaunch");
+    }
+    if (plain) cudaGraphExecDestroy(plain);
+    if (s != STEPS_OK) return s;
+    if (t_out) STEPS_CUDA(cudaMemcpyAsync(t_out, c->sc + SC_T, sizeof(double), cudaMemcpyDefault, c->st));
+    return sync_and_check(c);
+}
+
 steps_status steps_get_state(steps_ctx *c, double *pos, double *vel, double *acc, double *t,
                              double *a) {
     if (!c) {

@@ -7,6 +7,7 @@
 // round trip and can be captured in a CUDA graph.
 #include <cfloat>
 #include <cuda_runtime.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 #include "steps_internal.h"
@@ -85,6 +86,56 @@ __global__ void rk4_kernel(double *sc, Cosmo c) {
     sc[SC_T] += dt;
     sc[SC_STEP] += 1.0;
     sc[SC_RUN] += 1.0;
+}
+
+// Eq. 12, first level: per block, min over its particles of q_i = 2 eta_i eps / |A_i|
+// (eta_i = 2.8 h_i), A_i the acceleration the kick applies at the current state
+// (same expression as kick_kernel).  |A_i| = 0 sets no limit (q = +inf).
+__global__ void timestep_partial(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                                 const double *__restrict__ z, const double *__restrict__ vx,
+                                 const double *__restrict__ vy, const double *__restrict__ vz,
+                                 const double *__restrict__ ax, const double *__restrict__ ay,
+                                 const double *__restrict__ az, const double *__restrict__ h,
+                                 const double *__restrict__ sc, Cosmo c, double eps,
+                                 double *__restrict__ part) {
+    __shared__ double s[256];
+    double q = CUDART_INF;
+    const double a = sc[SC_A], H = sc[SC_H];
+    const double ia3 = 1.0 / (a * a * a);
+    const double bg = 0.5 * c.Om * c.H0 * c.H0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double Ax = ax[i], Ay = ay[i], Az = az[i];
+        if (c.comoving) {
+            Ax = ax[i] * ia3 - 2.0 * H * vx[i] + bg * x[i] * ia3;
+            Ay = ay[i] * ia3 - 2.0 * H * vy[i] + bg * y[i] * ia3;
+            Az = az[i] * ia3 - 2.0 * H * vz[i] + bg * z[i] * ia3;
+        }
+        const double amag = sqrt(Ax * Ax + Ay * Ay + Az * Az);
+        if (amag > 0.0) q = fmin(q, 2.0 * (2.8 * h[i]) * eps / amag);
+    }
+    s[threadIdx.x] = q;
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (threadIdx.x < o) s[threadIdx.x] = fmin(s[threadIdx.x], s[threadIdx.x + o]);
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) part[blockIdx.x] = s[0];
+}
+
+// Eq. 12, second level: dt = min(dt_max, sqrt(min q)), limited to t_end - t
+// (never below 0) when t_end is finite; becomes the next step's dt.
+__global__ void timestep_finish(int nblk, const double *__restrict__ part, double dt_max, double t_end,
+                                double *sc) {
+    double q = CUDART_INF;
+    for (int b = 0; b < nblk; ++b) q = fmin(q, part[b]);
+    double dt = dt_max;
+    if (q < CUDART_INF && sqrt(q) < dt) dt = sqrt(q);
+    if (isfinite(t_end)) {
+        const double left = t_end - sc[SC_T];
+        if (left < dt) dt = left > 0.0 ? left : 0.0;
+    }
+    sc[SC_DT] = dt;
 }
 
 // dt of the next step of a multi-step run: dts[run index]; the index advances
@@ -219,6 +270,16 @@ cudaError_t launch_drift(int64_t n, double *x, double *y, double *z, const doubl
 
 cudaError_t launch_rk4(double *sc, const Cosmo &c, cudaStream_t st) {
     rk4_kernel<<<1, 1, 0, st>>>(sc, c);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_timestep(int64_t n, const double *x, const double *y, const double *z,
+                            const double *vx, const double *vy, const double *vz, const double *ax,
+                            const double *ay, const double *az, const double *h, double *sc,
+                            const Cosmo &c, double eps, double dt_max, double t_end, double *part,
+                            int nblk, cudaStream_t st) {
+    timestep_partial<<<nblk, 256, 0, st>>>(n, x, y, z, vx, vy, vz, ax, ay, az, h, sc, c, eps, part);
+    timestep_finish<<<1, 1, 0, st>>>(nblk, part, dt_max, t_end, sc);
     return cudaGetLastError();
 }
 

@@ -189,6 +189,13 @@ cudaError_t launch_drift(int64_t n, double *x, double *y, double *z, const doubl
                          const double *vy, const double *vz, const double *sc, cudaStream_t st);
 cudaError_t launch_rk4(double *sc, const Cosmo &c, cudaStream_t st);
 cudaError_t launch_set_dt(double *sc, const double *dts, cudaStream_t st);
+// Eq. 12: sc[SC_DT] = min(dt_max, min_i sqrt(2 (2.8 h_i) eps / |A_i|)), limited to
+// t_end - sc[SC_T] when t_end is finite; part holds nblk doubles of scratch.
+cudaError_t launch_timestep(int64_t n, const double *x, const double *y, const double *z,
+                            const double *vx, const double *vy, const double *vz, const double *ax,
+                            const double *ay, const double *az, const double *h, double *sc,
+                            const Cosmo &c, double eps, double dt_max, double t_end, double *part,
+                            int nblk, cudaStream_t st);
 
 // Deterministic FP64 reductions: out[0] = sum w*v^2/2, out[1..3] = sum w*v
 cudaError_t launch_kinetic(int64_t n, const double *vx, const double *vy, const double *vz,

@@ -27,7 +27,7 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
-    "steps_profile_read_far",
+    "steps_profile_read_far", "steps_timestep", "steps_kdk_run_adaptive",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
     "steps_ensemble_free", "steps_paircount",
@@ -76,6 +76,8 @@ def load(build_if_missing: bool = False):
     lib.steps_forces.argtypes = [P, P]
     lib.steps_kdk_step.argtypes = [P, D, P]
     lib.steps_kdk_run.argtypes = [P, I, P]
+    lib.steps_timestep.argtypes = [P, D, D, D, P]
+    lib.steps_kdk_run_adaptive.argtypes = [P, I, D, D, D, P]
     lib.steps_get_state.argtypes = [P, P, P, P, P, P]
     lib.steps_set_state.argtypes = [P, P, P, D, D]
     lib.steps_checkpoint_size.argtypes = [P, ctypes.POINTER(S)]
@@ -120,7 +122,8 @@ def load(build_if_missing: bool = False):
     lib.steps_num_variants.restype = I
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
-    for name in ["steps_init", "steps_forces", "steps_kdk_step", "steps_kdk_run", "steps_get_state",
+    for name in ["steps_init", "steps_forces", "steps_kdk_step", "steps_kdk_run", "steps_timestep",
+                 "steps_kdk_run_adaptive", "steps_get_state",
                  "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
@@ -227,6 +230,21 @@ def steps_kdk_step(ctx, dt: float, want_a: bool = False):
     a = ctypes.c_double()
     _check(load().steps_kdk_step(ctx, float(dt), ctypes.byref(a) if want_a else None))
     return a.value if want_a else None
+
+
+def steps_timestep(ctx, eps: float, dt_max: float, t_end: float = float("inf")) -> float:
+    """Eq. 12 at the current state (device reduction); returns dt."""
+    dt = ctypes.c_double()
+    _check(load().steps_timestep(ctx, float(eps), float(dt_max), float(t_end), ctypes.byref(dt)))
+    return dt.value
+
+
+def steps_kdk_run_adaptive(ctx, nsteps: int, eps: float, dt_max: float, t_end: float = float("inf")) -> float:
+    """nsteps KDK steps of Eq. 12 length, chosen on the device; returns the final t."""
+    t = ctypes.c_double()
+    _check(load().steps_kdk_run_adaptive(ctx, int(nsteps), float(eps), float(dt_max), float(t_end),
+                                         ctypes.byref(t)))
+    return t.value
 
 
 def steps_kdk_run(ctx, dts):
@@ -469,6 +487,12 @@ class Simulation:
 
     def run(self, dts):
         steps_kdk_run(self.ctx, dts)
+
+    def timestep(self, eps, dt_max, t_end=float("inf")):
+        return steps_timestep(self.ctx, eps, dt_max, t_end)
+
+    def run_adaptive(self, nsteps, eps, dt_max, t_end=float("inf")):
+        return steps_kdk_run_adaptive(self.ctx, nsteps, eps, dt_max, t_end)
 
     def state(self):
         pos, vel, acc = np.empty((self.n, 3)), np.empty((self.n, 3)), np.empty((self.n, 3))
