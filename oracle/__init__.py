@@ -9,7 +9,9 @@ Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
 
 The C part (``steps_oracle.c``) is compiled with gcc on first use; ``build()``
-does it explicitly.  The MLP oracle is plain numpy in ``mlp.py``.
+does it explicitly.  The MLP oracle is plain numpy in ``mlp.py``; the
+spherical-glass layout and placement (Eq. 14-18) are plain numpy in
+``glass.py``.
 """
 from __future__ import annotations
 
@@ -40,11 +42,13 @@ def build(force: bool = False) -> str:
 class Cosmo(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("H0", ctypes.c_double), ("Om", ctypes.c_double),
                 ("OL", ctypes.c_double), ("Or", ctypes.c_double), ("Ok", ctypes.c_double),
-                ("comoving", ctypes.c_int)]
+                ("comoving", ctypes.c_int), ("reversed", ctypes.c_int)]
 
 
-def cosmo(G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0, Ok=0.0, comoving=True) -> Cosmo:
-    return Cosmo(G, H0, Om, OL, Or, Ok, 1 if comoving else 0)
+def cosmo(G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0, Ok=0.0, comoving=True, reversed=False) -> Cosmo:
+    """reversed: Eq. 8 with gravity reversed (pair and background terms change
+    sign; comoving only), as in the glass relaxation of Sec. 3.1."""
+    return Cosmo(G, H0, Om, OL, Or, Ok, 1 if (comoving or reversed) else 0, 1 if reversed else 0)
 
 
 def _load():
@@ -161,7 +165,7 @@ class KDK:
         self.c = c
         self.a = ctypes.c_double(a0)
         self.t = ctypes.c_double(t0)
-        self.acc = pair_acc(self.pos, self.m, self.h, c.G)
+        self.acc = pair_acc(self.pos, self.m, self.h, -c.G if c.reversed else c.G)
 
     def step(self, dt: float):
         _load().oracle_kdk_step(self.m.size, _ptr(self.pos), _ptr(self.vel), _ptr(self.acc),

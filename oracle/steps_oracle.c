@@ -150,7 +150,12 @@ double oracle_pair_potential(int64_t n, const double *pos, const double *m, cons
 typedef struct {
     double G, H0, Om, OL, Or, Ok;
     int comoving; /* 0: static Newtonian (the paper's non-comoving mode), 1: Eq. 8 */
+    int reversed; /* 1: Eq. 8 with gravity reversed (glass relaxation, Sec. 3.1): the pair */
+                  /*    term and the background term both change sign                       */
 } oracle_cosmo;
+
+/* G of the pair term: -G when gravity is reversed. */
+static double pair_G(const oracle_cosmo *c) { return c->reversed ? -c->G : c->G; }
 
 double oracle_hubble(double a, const oracle_cosmo *c)
 {
@@ -189,7 +194,7 @@ static void kick(int64_t n, double *vel, const double *pos, const double *acc, d
     }
     double H = oracle_hubble(a, c);
     double rho_crit = 3.0 * c->H0 * c->H0 / (8.0 * M_PI * c->G);
-    double bg = 4.0 * M_PI * c->G / 3.0 * c->Om * rho_crit;
+    double bg = 4.0 * M_PI * pair_G(c) / 3.0 * c->Om * rho_crit;
     double a3 = a * a * a;
     for (int64_t k = 0; k < 3 * n; k++) {
         double A = acc[k] / a3 - 2.0 * H * vel[k] + bg * pos[k] / a3;
@@ -199,7 +204,8 @@ static void kick(int64_t n, double *vel, const double *pos, const double *acc, d
 
 /* ------------------------------------------------------------------ */
 /* Eq. 9-11: one kick-drift-kick step, U(dt) = K(dt/2) D(dt) K(dt/2).   */
-/* On entry acc holds the pair term at the current positions; on exit   */
+/* On entry acc holds the pair term at the current positions (with the  */
+/* sign of gravity of c, see pair_G); on exit                            */
 /* it holds the pair term at the new positions (one force evaluation    */
 /* per step).  *a and *t advance by RK4 over dt.  In each half-kick the  */
 /* friction and background use a, H at that half-kick's own time point  */
@@ -212,7 +218,7 @@ void oracle_kdk_step(int64_t n, double *pos, double *vel, double *acc, const dou
     for (int64_t k = 0; k < 3 * n; k++) pos[k] += vel[k] * dt;  /* D(dt)   */
     if (c->comoving) *a = oracle_rk4_a(*a, dt, c);
     *t += dt;
-    oracle_pair_acc(n, pos, m, h, c->G, n, NULL, acc);        /* force   */
+    oracle_pair_acc(n, pos, m, h, pair_G(c), n, NULL, acc);   /* force   */
     kick(n, vel, pos, acc, 0.5 * dt, *a, c);                  /* K(dt/2) */
 }
 
@@ -236,7 +242,7 @@ double oracle_timestep(int64_t n, const double *pos, const double *vel, const do
     if (c->comoving) {
         double rho_crit = 3.0 * c->H0 * c->H0 / (8.0 * M_PI * c->G);
         H = oracle_hubble(a, c);
-        bg = 4.0 * M_PI * c->G / 3.0 * c->Om * rho_crit;
+        bg = 4.0 * M_PI * pair_G(c) / 3.0 * c->Om * rho_crit;
         a3 = a * a * a;
     }
     for (int64_t i = 0; i < n; i++) {
