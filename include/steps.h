@@ -46,7 +46,12 @@ typedef enum {
 
 typedef enum {
     STEPS_STATIC = 0,   /* static, non-comoving Newtonian background (the paper's proper-coordinate mode) */
-    STEPS_COMOVING = 1  /* spherical comoving equation of motion, Eq. 8 */
+    STEPS_COMOVING = 1, /* spherical comoving equation of motion, Eq. 8 */
+    STEPS_COMOVING_REVERSED = 2 /* Eq. 8 with gravity reversed, as for relaxing a glass (Sec. 3.1): the
+                                   pair term and the background term both change sign, so a uniform
+                                   sphere stays in equilibrium; a(t) still follows Eq. 1 (an
+                                   Einstein-de Sitter background: Om = 1, OL = 0).  Single
+                                   simulations only; steps_forces then returns the repulsive term. */
 } steps_mode;
 
 typedef enum {
@@ -265,6 +270,60 @@ steps_status steps_profile_read_far(steps_ctx *ctx, double *far_ms, int64_t *far
 steps_status steps_forces_noalloc(int64_t n, const double *pos, const double *mass,
                                   const double *soft, double h_min, double G, double *acc_out,
                                   void *cuda_stream);
+
+/*
+ * Spherical-glass initial conditions (Sec. 3.1, Eq. 14-18).  The real space is
+ * compactified onto the 3-sphere of diameter D_s by the inverse stereographic
+ * projection (Eq. 14: omega = 2 arctan(r / D_s)); the compactified space is
+ * cut into shells along omega, n_shell particles are placed uniformly in the
+ * compact volume of each shell and mapped back by Eq. 15, and each shell's
+ * particles carry m = rho_bar V_shell / n_shell (Eq. 16, V_shell the
+ * real-space volume).  Two slicings:
+ *   STEPS_GLASS_CONST_DOMEGA  -- n_radial shells of equal width in omega from
+ *       omega_c = 2 arctan(r_c / D_s) to omega_max = 2 arctan(R_sim / D_s);
+ *       the ball r < r_c holds N_inner = floor((4 pi / 3) r_c^3 rho_bar / m_inner)
+ *       equal-mass particles (Eq. 17), m_inner = the first shell's particle
+ *       mass, placed uniformly in real space;
+ *   STEPS_GLASS_CONST_VOLUME  -- n_radial shells of equal compact volume from
+ *       omega = 0 to omega_max, edges from Eq. 18 solved numerically.
+ * The glass itself is made by relaxing these positions under reversed gravity
+ * (steps_init with mode STEPS_COMOVING_REVERSED, Om = 1, OL = 0).
+ */
+typedef enum { STEPS_GLASS_CONST_DOMEGA = 0, STEPS_GLASS_CONST_VOLUME = 1 } steps_glass_scheme;
+
+typedef struct {
+    int scheme;       /* steps_glass_scheme */
+    double D_s;       /* diameter of the hypersphere (Eq. 14-15) */
+    double R_sim;     /* real-space radius of the simulated volume */
+    int n_radial;     /* shells (outside the inner ball for STEPS_GLASS_CONST_DOMEGA) */
+    int64_t n_shell;  /* particles per shell */
+    double r_c;       /* STEPS_GLASS_CONST_DOMEGA: radius of the united inner ball, 0 < r_c < R_sim */
+    double rho_bar;   /* mean matter density Om rho_crit of Eq. 16 */
+} steps_glass_spec;
+
+/*
+ * The layout of a spec: total particle count, inner-ball count and mass (0
+ * for STEPS_GLASS_CONST_VOLUME), shell edges in omega [n_radial + 1] and the
+ * particle mass of each shell [n_radial].  Host outputs, any may be NULL.
+ * EINVAL for a non-positive or non-finite size, an unknown scheme, or r_c
+ * outside (0, R_sim) in the constant delta-omega scheme.
+ */
+steps_status steps_glass_layout(const steps_glass_spec *spec, int64_t *n_total, int64_t *n_inner,
+                                double *m_inner, double *omega_edges, double *shell_mass);
+
+/*
+ * Place the n = n_total particles of a spec from the caller's uniform random
+ * numbers u [n][3] in [0, 1): u[k][0] picks omega inside the particle's shell
+ * (by the compact-volume law) or the radius inside the inner ball, u[k][1] the
+ * cosine of the polar angle (1 - 2u), u[k][2] the azimuth (2 pi u).  Writes
+ * pos [n][3] and mass [n]: the inner ball's particles first, then n_shell per
+ * shell, innermost first.  u, pos and mass may be host or device pointers;
+ * the call allocates device scratch of 7n + 2 n_radial + 1 doubles for its
+ * duration and synchronises the stream.  EINVAL as steps_glass_layout, or if
+ * n is not the layout's count.
+ */
+steps_status steps_glass_place(const steps_glass_spec *spec, int64_t n, const double *u, double *pos,
+                               double *mass, void *cuda_stream);
 
 /*
  * Ensembles: many independent simulations of uneven N and differing

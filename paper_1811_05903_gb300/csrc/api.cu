@@ -496,7 +496,7 @@ steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const dou
         return STEPS_EINVAL;
     }
     steps_config c = cfg ? *cfg : steps_default_config();
-    if (c.mode != STEPS_STATIC && c.mode != STEPS_COMOVING) {
+    if (c.mode != STEPS_STATIC && c.mode != STEPS_COMOVING && c.mode != STEPS_COMOVING_REVERSED) {
         set_error("unknown mode %d", c.mode);
         return STEPS_EINVAL;
     }
@@ -514,7 +514,7 @@ steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const dou
         return STEPS_EINVAL;
     }
     if (!std::isfinite(c.G) || !std::isfinite(t0) ||
-        (c.mode == STEPS_COMOVING && (!(a0 > 0.0) || !std::isfinite(a0) || !std::isfinite(c.H0)))) {
+        (c.mode != STEPS_STATIC && (!(a0 > 0.0) || !std::isfinite(a0) || !std::isfinite(c.H0)))) {
         set_error("G, t0, H0 and a0 must be finite (a0 > 0 in comoving mode)");
         return STEPS_EINVAL;
     }
@@ -525,7 +525,8 @@ steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const dou
     }
     ctx->n = n;
     ctx->cfg = c;
-    ctx->cosmo = Cosmo{c.G, c.H0, c.Om, c.OL, c.Or, c.Ok, c.mode == STEPS_COMOVING ? 1 : 0};
+    const bool rev = c.mode == STEPS_COMOVING_REVERSED;
+    ctx->cosmo = Cosmo{rev ? -c.G : c.G, c.H0, c.Om, c.OL, c.Or, c.Ok, c.mode != STEPS_STATIC ? 1 : 0, rev ? 1 : 0};
     if (cuda_stream) {
         ctx->st = (cudaStream_t)cuda_stream;
     } else {

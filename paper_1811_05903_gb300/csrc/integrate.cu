@@ -45,7 +45,7 @@ __global__ void kick_kernel(int64_t n, const double *__restrict__ x, const doubl
     }
     const double a = sc[SC_A], H = sc[SC_H];
     const double ia3 = 1.0 / (a * a * a);
-    const double bg = 0.5 * c.Om * c.H0 * c.H0;
+    const double bg = (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
     const double Ax = ax[i] * ia3 - 2.0 * H * vx[i] + bg * x[i] * ia3;
     const double Ay = ay[i] * ia3 - 2.0 * H * vy[i] + bg * y[i] * ia3;
     const double Az = az[i] * ia3 - 2.0 * H * vz[i] + bg * z[i] * ia3;
@@ -102,7 +102,7 @@ __global__ void timestep_partial(int64_t n, const double *__restrict__ x, const 
     double q = CUDART_INF;
     const double a = sc[SC_A], H = sc[SC_H];
     const double ia3 = 1.0 / (a * a * a);
-    const double bg = 0.5 * c.Om * c.H0 * c.H0;
+    const double bg = (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double Ax = ax[i], Ay = ay[i], Az = az[i];

@@ -178,8 +178,9 @@ cudaError_t gather_i64(int64_t n, const unsigned int *vals, const int64_t *in, i
 enum { SC_T = 0, SC_A = 1, SC_H = 2, SC_DT = 3, SC_STEP = 4, SC_RUN = 5, SC_COUNT = 8 };
 
 struct Cosmo {
-    double G, H0, Om, OL, Or, Ok;
+    double G, H0, Om, OL, Or, Ok;  // G is the pair term's constant: -G when gravity is reversed
     int comoving;
+    int reversed;                  // 1: the background term of Eq. 8 changes sign too
 };
 
 cudaError_t launch_kick(int64_t n, const double *x, const double *y, const double *z, double *vx,

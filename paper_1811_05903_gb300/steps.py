@@ -18,7 +18,8 @@ from . import build as _build
 _lib = None
 
 STEPS_OK, STEPS_EINVAL, STEPS_ENOMEM, STEPS_ECUDA, STEPS_ETIMEOUT, STEPS_ENONFINITE, STEPS_EUNSUPPORTED = range(7)
-STEPS_STATIC, STEPS_COMOVING = 0, 1
+STEPS_STATIC, STEPS_COMOVING, STEPS_COMOVING_REVERSED = 0, 1, 2
+STEPS_GLASS_CONST_DOMEGA, STEPS_GLASS_CONST_VOLUME = 0, 1
 STEPS_F32_COMP, STEPS_F32_NAIVE, STEPS_F64 = 0, 1, 2
 
 HEADER_SYMBOLS = [
@@ -27,7 +28,8 @@ HEADER_SYMBOLS = [
     "steps_checkpoint_load", "steps_diagnostics", "steps_size", "steps_free", "steps_strerror",
     "steps_last_error", "steps_set_wait_limit", "steps_set_memory_limit", "steps_num_variants",
     "steps_variant_name", "steps_forces_subset", "steps_profile_enable", "steps_profile_read",
-    "steps_profile_read_far", "steps_timestep", "steps_kdk_run_adaptive",
+    "steps_profile_read_far", "steps_timestep", "steps_kdk_run_adaptive", "steps_glass_layout",
+    "steps_glass_place",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
     "steps_ensemble_free", "steps_paircount",
@@ -45,6 +47,12 @@ class StepsError(RuntimeError):
 
 _STATUS_NAMES = {0: "STEPS_OK", 1: "STEPS_EINVAL", 2: "STEPS_ENOMEM", 3: "STEPS_ECUDA",
                  4: "STEPS_ETIMEOUT", 5: "STEPS_ENONFINITE", 6: "STEPS_EUNSUPPORTED"}
+
+
+class steps_glass_spec(ctypes.Structure):
+    _fields_ = [("scheme", ctypes.c_int), ("D_s", ctypes.c_double), ("R_sim", ctypes.c_double),
+                ("n_radial", ctypes.c_int), ("n_shell", ctypes.c_int64), ("r_c", ctypes.c_double),
+                ("rho_bar", ctypes.c_double)]
 
 
 class steps_config(ctypes.Structure):
@@ -77,6 +85,8 @@ def load(build_if_missing: bool = False):
     lib.steps_kdk_step.argtypes = [P, D, P]
     lib.steps_kdk_run.argtypes = [P, I, P]
     lib.steps_timestep.argtypes = [P, D, D, D, P]
+    lib.steps_glass_layout.argtypes = [ctypes.POINTER(steps_glass_spec), P, P, P, P, P]
+    lib.steps_glass_place.argtypes = [ctypes.POINTER(steps_glass_spec), I64, P, P, P, P]
     lib.steps_kdk_run_adaptive.argtypes = [P, I, D, D, D, P]
     lib.steps_get_state.argtypes = [P, P, P, P, P, P]
     lib.steps_set_state.argtypes = [P, P, P, D, D]
@@ -123,7 +133,7 @@ def load(build_if_missing: bool = False):
     lib.steps_variant_name.argtypes = [I]
     lib.steps_variant_name.restype = ctypes.c_char_p
     for name in ["steps_init", "steps_forces", "steps_kdk_step", "steps_kdk_run", "steps_timestep",
-                 "steps_kdk_run_adaptive", "steps_get_state",
+                 "steps_kdk_run_adaptive", "steps_glass_layout", "steps_glass_place", "steps_get_state",
                  "steps_set_state", "steps_checkpoint_size", "steps_checkpoint_save",
                  "steps_checkpoint_load", "steps_diagnostics", "steps_set_wait_limit",
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
@@ -245,6 +255,34 @@ def steps_kdk_run_adaptive(ctx, nsteps: int, eps: float, dt_max: float, t_end: f
     _check(load().steps_kdk_run_adaptive(ctx, int(nsteps), float(eps), float(dt_max), float(t_end),
                                          ctypes.byref(t)))
     return t.value
+
+
+def glass_spec(scheme, D_s, R_sim, n_radial, n_shell, r_c=0.0, rho_bar=1.0) -> steps_glass_spec:
+    return steps_glass_spec(int(scheme), float(D_s), float(R_sim), int(n_radial), int(n_shell), float(r_c),
+                            float(rho_bar))
+
+
+def steps_glass_layout(spec: steps_glass_spec):
+    """(n_total, n_inner, m_inner, omega edges [n_radial + 1], shell masses [n_radial])."""
+    n, ni, mi = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    edges = np.empty(spec.n_radial + 1)
+    masses = np.empty(spec.n_radial)
+    _check(load().steps_glass_layout(ctypes.byref(spec), ctypes.byref(n), ctypes.byref(ni), ctypes.byref(mi),
+                                     ptr(edges), ptr(masses)))
+    return n.value, ni.value, mi.value, edges, masses
+
+
+def steps_glass_place(spec: steps_glass_spec, u, pos=None, mass=None, stream=None):
+    """Positions [n][3] and masses [n] from uniforms u [n][3] (numpy or CUDA tensors)."""
+    if isinstance(u, np.ndarray):
+        u = np.ascontiguousarray(u, dtype=np.float64)
+    n = int(u.shape[0])
+    if pos is None:
+        pos = np.empty((n, 3))
+    if mass is None:
+        mass = np.empty(n)
+    _check(load().steps_glass_place(ctypes.byref(spec), n, ptr(u), ptr(pos), ptr(mass), stream))
+    return pos, mass
 
 
 def steps_kdk_run(ctx, dts):
