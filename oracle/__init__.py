@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY.  The plain, slow, obviously-correct definition of
 what the GPU library computes: the spline-softened pair sum (Eq. 3, 4, 8), the
 mass-tied softening (Eq. 7), the kick-drift-kick step (Eq. 9-11) with an RK4
-scale factor (Eq. 1), the adaptive step length (Eq. 12), the pair potential,
+scale factor (Eq. 1), the adaptive step length (Eq. 12), the periodic image sum
+(Eq. 2, Eq. 5) and its KDK step, the pair potential,
 pair counts and the emulator MLP.
 Only the test suite, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
 ``bench.py`` may import this package.  It shares no code with the CUDA path.
@@ -70,6 +71,8 @@ def _load():
         lib.oracle_rk4_a.argtypes = [D, D, ctypes.POINTER(Cosmo)]
         lib.oracle_kdk_step.argtypes = [I64, P, P, P, P, P, D, P, P, ctypes.POINTER(Cosmo)]
         lib.oracle_kinetic.argtypes = [I64, P, P, P, P]
+        lib.oracle_pair_acc_periodic.argtypes = [I64, P, P, P, D, D, ctypes.c_int, I64, P, P]
+        lib.oracle_kdk_step_periodic.argtypes = [I64, P, P, P, P, P, D, P, P, D, D, D, D, D, D, D, ctypes.c_int]
         lib.oracle_timestep.restype = D
         lib.oracle_timestep.argtypes = [I64, P, P, P, P, D, D, D, D, ctypes.POINTER(Cosmo)]
         lib.oracle_paircount.argtypes = [I64, P, ctypes.c_int, P, P]
@@ -119,6 +122,45 @@ def pair_acc(pos, m, h, G: float = 1.0, targets=None) -> np.ndarray:
     out = np.empty((nt, 3), dtype=np.float64)
     _load().oracle_pair_acc(n, _ptr(pos), _ptr(m), _ptr(h), float(G), nt, tp, _ptr(out))
     return out
+
+
+def pair_acc_periodic(pos, m, h, G: float, L: float, images: int = 0, targets=None) -> np.ndarray:
+    """Periodic pair term (Eq. 2 with Eq. 5): images = 0 sums every image with
+    |x_i - x_j - nL| < 2.6 L, images = 1 keeps the leading (nearest) one."""
+    pos = _f64(pos, (-1, 3))
+    m, h = _f64(m), _f64(h)
+    n = pos.shape[0]
+    if targets is None:
+        nt, tp = n, None
+    else:
+        targets = np.ascontiguousarray(targets, dtype=np.int64)
+        nt, tp = targets.size, _ptr(targets)
+    out = np.empty((nt, 3), dtype=np.float64)
+    _load().oracle_pair_acc_periodic(n, _ptr(pos), _ptr(m), _ptr(h), float(G), float(L), int(images), nt, tp,
+                                     _ptr(out))
+    return out
+
+
+class KDKPeriodic:
+    """Literal KDK (Eq. 9-11) of the periodic comoving equation of motion (Eq. 2):
+    no background term, positions wrapped into [0, L)^3 after each drift."""
+
+    def __init__(self, pos, vel, m, h, L: float, images: int = 0, G=1.0, H0=1.0, Om=1.0, OL=0.0, Or=0.0,
+                 Ok=0.0, a0: float = 1.0, t0: float = 0.0):
+        self.pos = _f64(pos, (-1, 3)).copy()
+        self.vel = _f64(vel, (-1, 3)).copy()
+        self.m = _f64(m).copy()
+        self.h = _f64(h).copy()
+        self.L, self.images = float(L), int(images)
+        self.par = (float(G), float(H0), float(Om), float(OL), float(Or), float(Ok))
+        self.a = ctypes.c_double(a0)
+        self.t = ctypes.c_double(t0)
+        self.acc = pair_acc_periodic(self.pos, self.m, self.h, G, L, images)
+
+    def step(self, dt: float):
+        _load().oracle_kdk_step_periodic(self.m.size, _ptr(self.pos), _ptr(self.vel), _ptr(self.acc),
+                                         _ptr(self.m), _ptr(self.h), float(dt), ctypes.byref(self.a),
+                                         ctypes.byref(self.t), *self.par, self.L, self.images)
 
 
 def pair_potential(pos, m, h, G: float = 1.0) -> float:

@@ -24,6 +24,9 @@
  *   oracle_rk4_a         -- flat LambdaCDM closed form t(a)
  *   oracle_kdk_step      -- Kepler orbit (period, second order), energy
  *                           conservation, uniform comoving sphere at rest
+ *   oracle_pair_acc_periodic -- a cubic lattice feels no force, translation
+ *                           invariance, third law, quasi-periodic = open sum
+ *                           for a compact cluster, the cut at 2.6 L
  *   oracle_timestep      -- closed forms: a bound pair, a lone particle at
  *                           rest off-centre (background term) and a moving
  *                           one (friction term); dt_max and t_end limits
@@ -220,6 +223,89 @@ void oracle_kdk_step(int64_t n, double *pos, double *vel, double *acc, const dou
     *t += dt;
     oracle_pair_acc(n, pos, m, h, pair_G(c), n, NULL, acc);   /* force   */
     kick(n, vel, pos, acc, 0.5 * dt, *a, c);                  /* K(dt/2) */
+}
+
+/* ------------------------------------------------------------------ */
+/* Periodic pair term (Sec. 2.2, Eq. 2 with the image sum of Eq. 5):      */
+/*   acc_i = -G sum_{j != i} m_j sum_n F(|d_n|, h_i + h_j) d_n / |d_n|,    */
+/*   d_n = (x_i - x_j) - n L,                                            */
+/* images = 0: every integer triplet n with |d_n| < 2.6 L (the cut of    */
+/*             Sec. 2.2);                                                */
+/* images = 1: quasi-periodic, the leading term only: the one n with     */
+/*             d_n in [-L/2, L/2)^3, i.e. n = floor(d_0 / L + 1/2) per   */
+/*             component.                                                */
+/* Written without contraction: dx = (xi - xj) - nx * L, r2 = dx*dx +    */
+/* dy*dy + dz*dz, compared with (2.6 L)^2.                               */
+/* ------------------------------------------------------------------ */
+static void add_image(double *acc, double dx, double dy, double dz, double mj, double H, double G)
+{
+    double r = sqrt(dx * dx + dy * dy + dz * dz);
+    if (r == 0.0) return;
+    double f = G * mj * oracle_spline_F(r, H) / r;
+    acc[0] -= f * dx;
+    acc[1] -= f * dy;
+    acc[2] -= f * dz;
+}
+
+void oracle_pair_acc_periodic(int64_t n, const double *pos, const double *m, const double *h, double G,
+                              double L, int images, int64_t nt, const int64_t *targets, double *out)
+{
+    const double cut = 2.6 * L, cut2 = cut * cut;
+#pragma omp parallel for schedule(dynamic, 4)
+    for (int64_t t = 0; t < nt; t++) {
+        int64_t i = targets ? targets[t] : t;
+        double acc[3] = {0.0, 0.0, 0.0};
+        for (int64_t j = 0; j < n; j++) {
+            if (j == i) continue;
+            double d0x = pos[3 * i] - pos[3 * j];
+            double d0y = pos[3 * i + 1] - pos[3 * j + 1];
+            double d0z = pos[3 * i + 2] - pos[3 * j + 2];
+            double H = h[i] + h[j];
+            if (images == 1) {
+                double nx = floor(d0x / L + 0.5), ny = floor(d0y / L + 0.5), nz = floor(d0z / L + 0.5);
+                add_image(acc, d0x - nx * L, d0y - ny * L, d0z - nz * L, m[j], H, G);
+                continue;
+            }
+            long ax = (long)floor((d0x - cut) / L), bx = (long)ceil((d0x + cut) / L);
+            long ay = (long)floor((d0y - cut) / L), by = (long)ceil((d0y + cut) / L);
+            long az = (long)floor((d0z - cut) / L), bz = (long)ceil((d0z + cut) / L);
+            for (long nx = ax; nx <= bx; nx++)
+                for (long ny = ay; ny <= by; ny++)
+                    for (long nz = az; nz <= bz; nz++) {
+                        double dx = d0x - (double)nx * L;
+                        double dy = d0y - (double)ny * L;
+                        double dz = d0z - (double)nz * L;
+                        double r2 = dx * dx + dy * dy + dz * dz;
+                        if (r2 < cut2) add_image(acc, dx, dy, dz, m[j], H, G);
+                    }
+        }
+        out[3 * t] = acc[0];
+        out[3 * t + 1] = acc[1];
+        out[3 * t + 2] = acc[2];
+    }
+}
+
+/* One KDK step of the periodic comoving equation of motion (Eq. 2):      */
+/* A = acc / a^3 - 2 H v (no background term), positions wrapped into    */
+/* [0, L)^3 after the drift, acc from oracle_pair_acc_periodic.           */
+void oracle_kdk_step_periodic(int64_t n, double *pos, double *vel, double *acc, const double *m,
+                              const double *h, double dt, double *a, double *t, double G, double H0,
+                              double Om, double OL, double Or, double Ok, double L, int images)
+{
+    oracle_cosmo c = {G, H0, Om, OL, Or, Ok, 1, 0};
+    for (int half = 0; half < 2; half++) {
+        if (half == 1) {
+            for (int64_t k = 0; k < 3 * n; k++) {
+                pos[k] += vel[k] * dt;
+                pos[k] -= L * floor(pos[k] / L);
+            }
+            *a = oracle_rk4_a(*a, dt, &c);
+            *t += dt;
+            oracle_pair_acc_periodic(n, pos, m, h, G, L, images, n, NULL, acc);
+        }
+        double H = oracle_hubble(*a, &c), a3 = (*a) * (*a) * (*a);
+        for (int64_t k = 0; k < 3 * n; k++) vel[k] += 0.5 * dt * (acc[k] / a3 - 2.0 * H * vel[k]);
+    }
 }
 
 /* ------------------------------------------------------------------ */
