@@ -47,11 +47,17 @@ typedef enum {
 typedef enum {
     STEPS_STATIC = 0,   /* static, non-comoving Newtonian background (the paper's proper-coordinate mode) */
     STEPS_COMOVING = 1, /* spherical comoving equation of motion, Eq. 8 */
-    STEPS_COMOVING_REVERSED = 2 /* Eq. 8 with gravity reversed, as for relaxing a glass (Sec. 3.1): the
+    STEPS_COMOVING_REVERSED = 2, /* Eq. 8 with gravity reversed, as for relaxing a glass (Sec. 3.1): the
                                    pair term and the background term both change sign, so a uniform
                                    sphere stays in equilibrium; a(t) still follows Eq. 1 (an
                                    Einstein-de Sitter background: Om = 1, OL = 0).  Single
                                    simulations only; steps_forces then returns the repulsive term. */
+    STEPS_PERIODIC = 3  /* periodic comoving equation of motion, Eq. 2: pair term / a^3 - 2 H v with
+                           the image sum of Eq. 5 in a cubic box of side `box` (every image n with
+                           |x_i - x_j - nL| < 2.6 L, or with images = 1 only the leading one, the n
+                           with x_i - x_j - nL in [-L/2, L/2)^3); positions are wrapped into
+                           [0, L)^3.  STEPS_F32_COMP or STEPS_F64 only; single simulations only;
+                           steps_forces_subset and the potential energy are not available. */
 } steps_mode;
 
 typedef enum {
@@ -68,6 +74,8 @@ typedef struct {
     int prec;                 /* steps_prec */
     int resort_every;         /* re-sort particles spatially every this many steps (<=0: default 8) */
     int tile_override;        /* 0 = autotuned force-kernel variant; k>0 selects variant k-1 */
+    double box;               /* STEPS_PERIODIC: side L of the periodic box */
+    int images;               /* STEPS_PERIODIC: 0 = image sum cut at 2.6 L (Eq. 5), 1 = quasi-periodic */
 } steps_config;
 
 typedef struct steps_ctx steps_ctx;

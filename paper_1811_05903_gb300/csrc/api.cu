@@ -255,7 +255,23 @@ steps_status compute_forces(steps_ctx *c) {
             STEPS_CUDA(cudaEventCreate(&f1));
         }
     }
-    if (c->cfg.prec == STEPS_F64) {
+    if (c->cosmo.periodic) {
+        // Eq. 2 with the image sum of Eq. 5
+        if (c->cfg.prec == STEPS_F64) {
+            if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
+            STEPS_CUDA(launch_periodic_f64(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, c->cosmo.box,
+                                           c->cfg.images, c->ax, c->ay, c->az, c->st));
+            c->kernel_launches += 1;
+        } else {
+            launch_stage(c->stg, c->x, c->y, c->z, c->m, c->h, c->st);
+            STEPS_CUDA(cudaGetLastError());
+            if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
+            STEPS_CUDA(launch_periodic_f32(c->stg, c->x, c->y, c->z, c->cosmo.box, c->cfg.images, c->cosmo.G,
+                                           c->nr.item_part, c->ax, c->ay, c->az, c->st));
+            c->kernel_launches += 3;  // stage, periodic, reduce
+        }
+        if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
+    } else if (c->cfg.prec == STEPS_F64) {
         if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
         STEPS_CUDA(launch_force_f64(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, 0, c->n, c->ax,
                                     c->ay, c->az, c->st));
@@ -331,7 +347,10 @@ steps_status issue_step(steps_ctx *c, bool do_sort) {
     c->kernel_launches += 4;  // kick, drift, rk4, kick
     STEPS_CUDA(launch_kick(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->ax, c->ay, c->az, c->sc,
                            c->cosmo, c->st));
-    STEPS_CUDA(launch_drift(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->sc, c->st));
+    if (c->cosmo.periodic)
+        STEPS_CUDA(launch_drift_wrap(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->sc, c->cosmo.box, c->st));
+    else
+        STEPS_CUDA(launch_drift(c->n, c->x, c->y, c->z, c->vx, c->vy, c->vz, c->sc, c->st));
     STEPS_CUDA(launch_rk4(c->sc, c->cosmo, c->st));
     if (do_sort) STEPS_TRY(resort(c));
     STEPS_TRY(compute_forces(c));
@@ -422,6 +441,9 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
 
     // upload (caller order == initial internal order)
     STEPS_TRY(load3(c, pos, c->x, c->y, c->z, false));
+    if (c->cosmo.periodic) {
+        for (double *v : {c->x, c->y, c->z}) STEPS_CUDA(launch_wrap(n, v, c->cosmo.box, c->st));
+    }
     if (vel) {
         STEPS_TRY(load3(c, vel, c->vx, c->vy, c->vz, false));
     } else {
@@ -456,7 +478,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_CUDA(cudaMemcpyAsync(c->sc, sc, sizeof(sc), cudaMemcpyHostToDevice, c->st));
     STEPS_TRY(configure_variant(c, pick_variant(c)));
     STEPS_TRY(resort(c));
-    if (c->cfg.prec != STEPS_F64 && c->cfg.tile_override == 0) STEPS_TRY(autotune(c));
+    if (c->cfg.prec != STEPS_F64 && c->cfg.tile_override == 0 && !c->cosmo.periodic) STEPS_TRY(autotune(c));
     STEPS_TRY(compute_forces(c));
     return sync_and_check(c);
 }
@@ -496,9 +518,20 @@ steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const dou
         return STEPS_EINVAL;
     }
     steps_config c = cfg ? *cfg : steps_default_config();
-    if (c.mode != STEPS_STATIC && c.mode != STEPS_COMOVING && c.mode != STEPS_COMOVING_REVERSED) {
+    if (c.mode != STEPS_STATIC && c.mode != STEPS_COMOVING && c.mode != STEPS_COMOVING_REVERSED &&
+        c.mode != STEPS_PERIODIC) {
         set_error("unknown mode %d", c.mode);
         return STEPS_EINVAL;
+    }
+    if (c.mode == STEPS_PERIODIC) {
+        if (!(c.box > 0.0) || !std::isfinite(c.box) || (c.images != 0 && c.images != 1)) {
+            set_error("periodic mode needs a finite box > 0 and images 0 (cut at 2.6 L) or 1 (quasi-periodic)");
+            return STEPS_EINVAL;
+        }
+        if (c.prec == STEPS_F32_NAIVE) {
+            set_error("periodic mode runs with STEPS_F32_COMP or STEPS_F64");
+            return STEPS_EUNSUPPORTED;
+        }
     }
     if (c.prec < STEPS_F32_COMP || c.prec > STEPS_F64) {
         set_error("unknown precision %d", c.prec);
@@ -526,7 +559,9 @@ steps_status steps_init(steps_ctx **out, int64_t n, const double *pos, const dou
     ctx->n = n;
     ctx->cfg = c;
     const bool rev = c.mode == STEPS_COMOVING_REVERSED;
-    ctx->cosmo = Cosmo{rev ? -c.G : c.G, c.H0, c.Om, c.OL, c.Or, c.Ok, c.mode != STEPS_STATIC ? 1 : 0, rev ? 1 : 0};
+    const bool per = c.mode == STEPS_PERIODIC;
+    ctx->cosmo = Cosmo{rev ? -c.G : c.G, c.H0, c.Om, c.OL, c.Or, c.Ok, c.mode != STEPS_STATIC ? 1 : 0, rev ? 1 : 0,
+                       per ? 1 : 0, per ? c.box : 0.0};
     if (cuda_stream) {
         ctx->st = (cudaStream_t)cuda_stream;
     } else {
@@ -766,6 +801,9 @@ steps_status steps_set_state(steps_ctx *c, const double *pos, const double *vel,
         return STEPS_EINVAL;
     }
     STEPS_TRY(load3(c, pos, c->x, c->y, c->z, true));
+    if (c->cosmo.periodic) {
+        for (double *v : {c->x, c->y, c->z}) STEPS_CUDA(launch_wrap(c->n, v, c->cosmo.box, c->st));
+    }
     STEPS_TRY(load3(c, vel, c->vx, c->vy, c->vz, true));
     double sc[SC_COUNT];
     STEPS_CUDA(cudaMemcpyAsync(sc, c->sc, sizeof(sc), cudaMemcpyDeviceToHost, c->st));
@@ -859,6 +897,10 @@ steps_status steps_diagnostics(steps_ctx *c, double *ekin, double *epot, double 
         STEPS_CUDA(cudaMemcpyAsync(host, out, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->st));
         STEPS_CUDA(cudaStreamSynchronize(c->st));
     }
+    if (epot && c->cosmo.periodic) {
+        set_error("the pair potential is not available in periodic mode");
+        return STEPS_EUNSUPPORTED;
+    }
     if (epot) {
         STEPS_CUDA(launch_potential_f64(c->n, c->x, c->y, c->z, c->m, c->h, c->cosmo.G, c->tmp3,
                                         c->st));
@@ -880,6 +922,10 @@ steps_status steps_forces_subset(steps_ctx *c, int64_t nt, const int64_t *target
     if (!c || nt < 0 || (nt > 0 && (!targets || !acc_out))) {
         set_error("bad arguments to steps_forces_subset");
         return STEPS_EINVAL;
+    }
+    if (c->cosmo.periodic) {
+        set_error("steps_forces_subset computes the open-boundary sum; not available in periodic mode");
+        return STEPS_EUNSUPPORTED;
     }
     if (nt == 0) return STEPS_OK;
     if (nt > c->tgt_cap) {

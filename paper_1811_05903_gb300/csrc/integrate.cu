@@ -45,7 +45,7 @@ __global__ void kick_kernel(int64_t n, const double *__restrict__ x, const doubl
     }
     const double a = sc[SC_A], H = sc[SC_H];
     const double ia3 = 1.0 / (a * a * a);
-    const double bg = (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
+    const double bg = c.periodic ? 0.0 : (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
     const double Ax = ax[i] * ia3 - 2.0 * H * vx[i] + bg * x[i] * ia3;
     const double Ay = ay[i] * ia3 - 2.0 * H * vy[i] + bg * y[i] * ia3;
     const double Az = az[i] * ia3 - 2.0 * H * vz[i] + bg * z[i] * ia3;
@@ -102,7 +102,7 @@ __global__ void timestep_partial(int64_t n, const double *__restrict__ x, const 
     double q = CUDART_INF;
     const double a = sc[SC_A], H = sc[SC_H];
     const double ia3 = 1.0 / (a * a * a);
-    const double bg = (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
+    const double bg = c.periodic ? 0.0 : (c.reversed ? -0.5 : 0.5) * c.Om * c.H0 * c.H0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
          i += (int64_t)gridDim.x * blockDim.x) {
         double Ax = ax[i], Ay = ay[i], Az = az[i];
@@ -259,6 +259,38 @@ cudaError_t launch_kick(int64_t n, const double *x, const double *y, const doubl
                         double *vy, double *vz, const double *ax, const double *ay,
                         const double *az, const double *sc, const Cosmo &c, cudaStream_t st) {
     kick_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, x, y, z, vx, vy, vz, ax, ay, az, sc, c);
+    return cudaGetLastError();
+}
+
+__global__ void drift_wrap_kernel(int64_t n, double *__restrict__ x, double *__restrict__ y,
+                                  double *__restrict__ z, const double *__restrict__ vx,
+                                  const double *__restrict__ vy, const double *__restrict__ vz,
+                                  const double *__restrict__ sc, double box) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double dt = sc[SC_DT];
+    double *p[3] = {x, y, z};
+    const double *v[3] = {vx, vy, vz};
+    for (int k = 0; k < 3; ++k) {
+        const double q = __dadd_rn(p[k][i], __dmul_rn(v[k][i], dt));
+        p[k][i] = __dsub_rn(q, __dmul_rn(box, floor(__ddiv_rn(q, box))));
+    }
+}
+
+__global__ void wrap_kernel(int64_t n, double *__restrict__ v, double box) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) v[i] = __dsub_rn(v[i], __dmul_rn(box, floor(__ddiv_rn(v[i], box))));
+}
+
+cudaError_t launch_drift_wrap(int64_t n, double *x, double *y, double *z, const double *vx,
+                              const double *vy, const double *vz, const double *sc, double box,
+                              cudaStream_t st) {
+    drift_wrap_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, x, y, z, vx, vy, vz, sc, box);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wrap(int64_t n, double *v, double box, cudaStream_t st) {
+    if (n > 0) wrap_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, v, box);
     return cudaGetLastError();
 }
 

@@ -129,6 +129,26 @@ cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *par
                          const NearScratch &nr, double G, double *ax, double *ay, double *az,
                          cudaStream_t st);
 
+// Periodic pair term (Eq. 2 with Eq. 5).  FP32 path on the tile staging:
+// work items (target tile, chunk of source tiles) write FP64 partials
+// item_part [ntile * nchunk][3][T] (nchunk = periodic_chunks(ntile) <= 8),
+// then a reduction applies G into ax, ay, az (sorted order).
+struct PeriodicArgs {
+    const float4 *jdup, *rdup, *tbox_c, *tbox_e;
+    const double *x, *y, *z;  // FP64 sorted positions: decisions near the cut / half-box faces
+    double *item_part;
+    int64_t ntile, nchunk, n;
+    double L;
+    int images;
+};
+int64_t periodic_chunks(int64_t ntile);
+cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double *y, const double *z, double L,
+                                int images, double G, double *item_part, double *ax, double *ay, double *az,
+                                cudaStream_t st);
+cudaError_t launch_periodic_f64(int64_t n, const double *x, const double *y, const double *z, const double *m,
+                                const double *h, double G, double L, int images, double *ax, double *ay,
+                                double *az, cudaStream_t st);
+
 // FP64 comparison path: direct sum over sorted FP64 SoA, targets [i0, i1).
 cudaError_t launch_force_f64(int64_t n, const double *x, const double *y, const double *z,
                              const double *m, const double *h, double G, int64_t i0, int64_t i1,
@@ -181,11 +201,19 @@ struct Cosmo {
     double G, H0, Om, OL, Or, Ok;  // G is the pair term's constant: -G when gravity is reversed
     int comoving;
     int reversed;                  // 1: the background term of Eq. 8 changes sign too
+    int periodic;                  // 1: Eq. 2 (no background term), positions wrapped into [0, box)
+    double box;
 };
 
 cudaError_t launch_kick(int64_t n, const double *x, const double *y, const double *z, double *vx,
                         double *vy, double *vz, const double *ax, const double *ay,
                         const double *az, const double *sc, const Cosmo &c, cudaStream_t st);
+// Drift and wrap into [0, box)^3 (periodic mode): x += v dt; x -= box floor(x / box).
+cudaError_t launch_drift_wrap(int64_t n, double *x, double *y, double *z, const double *vx,
+                              const double *vy, const double *vz, const double *sc, double box,
+                              cudaStream_t st);
+// x -= box floor(x / box) for k < 3 n interleaved or n SoA values.
+cudaError_t launch_wrap(int64_t n, double *v, double box, cudaStream_t st);
 cudaError_t launch_drift(int64_t n, double *x, double *y, double *z, const double *vx,
                          const double *vy, const double *vz, const double *sc, cudaStream_t st);
 cudaError_t launch_rk4(double *sc, const Cosmo &c, cudaStream_t st);

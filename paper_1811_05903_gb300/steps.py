@@ -18,7 +18,7 @@ from . import build as _build
 _lib = None
 
 STEPS_OK, STEPS_EINVAL, STEPS_ENOMEM, STEPS_ECUDA, STEPS_ETIMEOUT, STEPS_ENONFINITE, STEPS_EUNSUPPORTED = range(7)
-STEPS_STATIC, STEPS_COMOVING, STEPS_COMOVING_REVERSED = 0, 1, 2
+STEPS_STATIC, STEPS_COMOVING, STEPS_COMOVING_REVERSED, STEPS_PERIODIC = 0, 1, 2, 3
 STEPS_GLASS_CONST_DOMEGA, STEPS_GLASS_CONST_VOLUME = 0, 1
 STEPS_F32_COMP, STEPS_F32_NAIVE, STEPS_F64 = 0, 1, 2
 
@@ -59,7 +59,7 @@ class steps_config(ctypes.Structure):
     _fields_ = [("G", ctypes.c_double), ("H0", ctypes.c_double), ("Om", ctypes.c_double),
                 ("OL", ctypes.c_double), ("Or", ctypes.c_double), ("Ok", ctypes.c_double),
                 ("mode", ctypes.c_int), ("prec", ctypes.c_int), ("resort_every", ctypes.c_int),
-                ("tile_override", ctypes.c_int)]
+                ("tile_override", ctypes.c_int), ("box", ctypes.c_double), ("images", ctypes.c_int)]
 
 
 def lib_path() -> str:
@@ -366,8 +366,8 @@ def steps_variants():
 
 
 def make_config(mode=STEPS_STATIC, prec=STEPS_F32_COMP, G=1.0, H0=1.0, Om=0.3, OL=0.7, Or=0.0,
-                Ok=0.0, resort_every=8, tile_override=0) -> steps_config:
-    return steps_config(G, H0, Om, OL, Or, Ok, mode, prec, resort_every, tile_override)
+                Ok=0.0, resort_every=8, tile_override=0, box=0.0, images=0) -> steps_config:
+    return steps_config(G, H0, Om, OL, Or, Ok, mode, prec, resort_every, tile_override, box, images)
 
 
 def steps_paircount(offsets, pos, centres, step, edge2, stream=None):
