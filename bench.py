@@ -211,6 +211,34 @@ def ensemble_throughput(stream, steps_mod, workloads_mod, timed_steps=4):
             "near_field_fraction": nnear / max(nall, 1)}
 
 
+def periodic_throughput(steps_mod, n=16384, L=1.0, seed=21):
+    """Periodic mode (Eq. 2 with Eq. 5): one FP32 force evaluation of a uniform
+    random box, cut image sum (|x - nL| < 2.6 L) and quasi-periodic; CUDA events
+    around the force kernels.  Work counted as N^2 x (4 pi / 3) 2.6^3 pair-image
+    terms for the cut sum (the expected number of images inside the cut sphere)
+    and N^2 for the quasi-periodic sum."""
+    rng = np.random.default_rng(seed)
+    pos = rng.random((n, 3)) * L
+    m = np.full(n, 1.0 / n)
+    h = np.full(n, 0.02 * L / n ** (1.0 / 3.0))
+    out = {"workload": "uniform random box, N=%d, L=%g, FP32 compensated" % (n, L)}
+    for images, name, terms in ((0, "cut_2p6L", 4.0 * math.pi / 3.0 * 2.6 ** 3), (1, "quasi", 1.0)):
+        cfg = steps_mod.make_config(mode=steps_mod.STEPS_PERIODIC, prec=steps_mod.STEPS_F32_COMP, Om=1.0, OL=0.0,
+                                    box=L, images=images)
+        sim = steps_mod.Simulation(pos, np.zeros_like(pos), m, soft=h, cfg=cfg)
+        steps_mod.steps_forces(sim.ctx)
+        steps_mod.steps_profile_read(sim.ctx, reset=True)
+        steps_mod.steps_profile_enable(sim.ctx, True)
+        for _ in range(2):
+            steps_mod.steps_forces(sim.ctx)
+        ms, launches, _ = steps_mod.steps_profile_read(sim.ctx, reset=True)
+        sim.close()
+        per = ms * 1e-3 / max(launches, 1)
+        out[name] = {"ms_per_evaluation": 1e3 * per, "pair_image_terms_per_s": terms * n * n / per,
+                     "fp32_tflops_at_20_flop": 20 * terms * n * n / per / 1e12}
+    return out
+
+
 def run_ours(args):
     import torch
     import torch.distributed as dist
@@ -343,6 +371,9 @@ def run_ours(args):
     ensemble = None
     if rank == 0 and not args.no_ensemble:
         ensemble = ensemble_throughput(stream, steps, workloads)
+    periodic = None
+    if rank == 0 and not args.no_periodic:
+        periodic = periodic_throughput(steps)
 
     if rank != 0:
         dist.destroy_process_group()
@@ -391,6 +422,7 @@ def run_ours(args):
         },
         "near_field_fraction": near_frac,
         "ensemble": ensemble,
+        "periodic": periodic,
         "wall_s_timed": wall,
     }
     print(json.dumps(line), flush=True)
@@ -410,6 +442,7 @@ def main():
     ap.add_argument("--ref-targets", type=int, default=512)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
+    ap.add_argument("--no-periodic", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

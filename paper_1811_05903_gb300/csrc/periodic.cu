@@ -14,10 +14,12 @@
 // FP32 separation, except within a thin band around the cut sphere (or the
 // half-box faces) where it is re-taken in FP64 from the FP64 positions with the
 // definition's own expression, so that it matches an FP64 evaluation of the
-// definition.  Each warp owns one target tile and a chunk of source tiles (a
-// work item); FP32 partial sums per (source tile, image) are Kahan-folded every
-// 8 sources and added into FP64 per-target sums, written per work item and
-// added in item order by the reduction kernel: deterministic.
+// definition; images whose whole tile box lies inside the cut sphere (or inside
+// the half-box region) skip the per-pair decision.  Each warp owns one target
+// tile and a chunk of source tiles (a work item); FP32 partial sums are
+// Kahan-folded every 8 sources across all images of a source tile and then
+// added into FP64 per-target sums, written per work item and added in item
+// order by the reduction kernel: deterministic.
 //
 // FP64 path.  One thread per target, every source, the image loops of the
 // definition in FP64 without contraction (the comparison variant).
@@ -149,9 +151,15 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
         }
         __syncwarp();
         const float4 cj = a.tbox_c[J], ej = a.tbox_e[J];
+        // compensated FP32 sums over all images and sources of tile J, one FP64 add per tile
+        float kh[KI][3], kc[KI][3];
+#pragma unroll
+        for (int t = 0; t < KI; ++t)
+            for (int c = 0; c < 3; ++c) kh[t][c] = kc[t][c] = 0.f;
         for (int k0 = 0; k0 < nimg; k0 += 32) {
-            // which images of tile J can hold a term for tile I (box test, FP64)
-            bool cand = false;
+            // which images of tile J can hold a term for tile I (box test, FP64), and
+            // which hold every pair of the two tiles (no per-pair decision needed)
+            bool cand = false, all_in = false;
             const int k = k0 + lane;
             if (k < nimg) {
                 int nx, ny, nz;
@@ -165,14 +173,19 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                     // some pair separation x_i - x_j - nL may lie in [-L/2, L/2]^3
                     cand = fabs(sx) <= 0.5 * a.L + wx + margin && fabs(sy) <= 0.5 * a.L + wy + margin &&
                            fabs(sz) <= 0.5 * a.L + wz + margin;
+                    all_in = fabs(sx) + wx < 0.5 * a.L - margin && fabs(sy) + wy < 0.5 * a.L - margin &&
+                             fabs(sz) + wz < 0.5 * a.L - margin;
                 } else {
                     const double gx = fmax(0.0, fabs(sx) - wx), gy = fmax(0.0, fabs(sy) - wy),
                                  gz = fmax(0.0, fabs(sz) - wz);
-                    const double cutm = 2.6 * a.L + margin;
+                    const double cutm = 2.6 * a.L + margin, cutn = 2.6 * a.L - margin;
                     cand = gx * gx + gy * gy + gz * gz < cutm * cutm;
+                    const double fx = fabs(sx) + wx, fy = fabs(sy) + wy, fz = fabs(sz) + wz;
+                    all_in = fx * fx + fy * fy + fz * fz < cutn * cutn;
                 }
             }
             unsigned mask = __ballot_sync(0xffffffffu, cand);
+            const unsigned inside = __ballot_sync(0xffffffffu, all_in);
             while (mask) {
                 const int b = __ffs(mask) - 1;
                 mask &= mask - 1;
@@ -185,6 +198,7 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                 const float hx = (float)dcx, hy = (float)dcy, hz = (float)dcz;
                 const float lx = (float)(dcx - hx), ly = (float)(dcy - hy), lz = (float)(dcz - hz);
                 const bool self_tile = (J == I) && (nx | ny | nz);
+                const bool decide = !((inside >> b) & 1u);
 #pragma unroll
                 for (int t = 0; t < KI; ++t) {
                     // -(s), s = fl(o_i + dc), and -(r_i + remainder(dc) + err(s))
@@ -195,7 +209,8 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                     const float nry = -((ryi[t] + ly) + e);
                     const float nzs = -two_sum_f(zi[t], hz, e);
                     const float nrz = -((rzi[t] + lz) + e);
-                    float hx_ = 0.f, hy_ = 0.f, hz_ = 0.f, cx_ = 0.f, cy_ = 0.f, cz_ = 0.f;
+                    float hx_ = kh[t][0], hy_ = kh[t][1], hz_ = kh[t][2];
+                    float cx_ = kc[t][0], cy_ = kc[t][1], cz_ = kc[t][2];
                     for (int f0 = 0; f0 < T; f0 += kFold) {
                         float px = 0.f, py = 0.f, pz = 0.f;
                         for (int j = f0; j < f0 + kFold; ++j) {
@@ -208,9 +223,11 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                             const float r2 = dx * dx + dy * dy + dz * dz;
                             if (!(r2 > 0.f) || B.z == 0.f) continue;            // self pair, padding
                             if (self_tile && j == lane * KI + t) continue;       // j == i: no self images
-                            bool in;
-                            bool ambiguous;
-                            if (a.images == 1) {
+                            bool in = true;
+                            bool ambiguous = false;
+                            if (!decide) {
+                                // every pair of this image is a term
+                            } else if (a.images == 1) {
                                 // x_i - x_j - nL = -d in [-L/2, L/2)  <=>  d in (-L/2, L/2]
                                 in = dx > -halfL && dx <= halfL && dy > -halfL && dy <= halfL && dz > -halfL &&
                                      dz <= halfL;
@@ -249,12 +266,18 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                         cz_ = (tt - hz_) - y;
                         hz_ = tt;
                     }
-                    acc[t][0] += (double)hx_ - (double)cx_;
-                    acc[t][1] += (double)hy_ - (double)cy_;
-                    acc[t][2] += (double)hz_ - (double)cz_;
+                    kh[t][0] = hx_;
+                    kh[t][1] = hy_;
+                    kh[t][2] = hz_;
+                    kc[t][0] = cx_;
+                    kc[t][1] = cy_;
+                    kc[t][2] = cz_;
                 }
             }
         }
+#pragma unroll
+        for (int t = 0; t < KI; ++t)
+            for (int c = 0; c < 3; ++c) acc[t][c] += (double)kh[t][c] - (double)kc[t][c];
     }
     double *P = a.item_part + (size_t)item * 3 * T;
 #pragma unroll
