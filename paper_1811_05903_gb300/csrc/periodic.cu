@@ -108,6 +108,76 @@ __device__ __noinline__ bool include_f64(double xi, double yi, double zi, double
     return r2 < __dmul_rn(cut, cut);
 }
 
+// The terms of one (source tile, image) for this lane's KI targets, added to
+// the targets' compensated sums (folded every kFold sources).  Each source is
+// read once from shared memory and used for all KI targets.  DECIDE: some
+// pairs of this image may fall outside the cut sphere (or the half-box
+// region), so every term is tested; otherwise every pair is a term.
+template <int KI, int T, bool DECIDE>
+__device__ __forceinline__ void image_terms(const float4 *__restrict__ S, const PeriodicArgs &a,
+                                            const float (&nxs)[KI], const float (&nys)[KI], const float (&nzs)[KI],
+                                            const float (&nrx)[KI], const float (&nry)[KI], const float (&nrz)[KI],
+                                            const float (&hI)[KI], const int64_t (&gi)[KI], int64_t J, int nx,
+                                            int ny, int nz, bool self_tile, int lane, float cut2, float halfL,
+                                            float L, float (&kh)[KI][3], float (&kc)[KI][3]) {
+    for (int f0 = 0; f0 < T; f0 += kFold) {
+        float px[KI], py[KI], pz[KI];
+#pragma unroll
+        for (int t = 0; t < KI; ++t) px[t] = py[t] = pz[t] = 0.f;
+#pragma unroll 2
+        for (int j = f0; j < f0 + kFold; ++j) {
+            const float4 A = S[2 * j], B = S[2 * j + 1];
+            const float4 RA = S[2 * T + 2 * j], RB = S[2 * T + 2 * j + 1];
+            if (B.z == 0.f) continue;  // padding source (zero mass)
+#pragma unroll
+            for (int t = 0; t < KI; ++t) {
+                // d = x_j + nL - x_i
+                const float dx = (A.x + nxs[t]) + (RA.x + nrx[t]);
+                const float dy = (A.z + nys[t]) + (RA.z + nry[t]);
+                const float dz = (B.x + nzs[t]) + (RB.x + nrz[t]);
+                const float r2 = dx * dx + dy * dy + dz * dz;
+                bool in = r2 > 0.f && !(self_tile && j == lane * KI + t);  // no self pair, no self images
+                if (DECIDE && in) {
+                    bool ambiguous;
+                    if (a.images == 1) {
+                        // x_i - x_j - nL = -d in [-L/2, L/2)  <=>  d in (-L/2, L/2]
+                        in = dx > -halfL && dx <= halfL && dy > -halfL && dy <= halfL && dz > -halfL && dz <= halfL;
+                        const float band = kFaceBand * L;
+                        ambiguous = fabsf(fabsf(dx) - halfL) < band || fabsf(fabsf(dy) - halfL) < band ||
+                                    fabsf(fabsf(dz) - halfL) < band;
+                    } else {
+                        in = r2 < cut2;
+                        ambiguous = fabsf(r2 - cut2) < kCutBand * cut2;
+                    }
+                    if (ambiguous) {
+                        const int64_t gj = J * T + j;
+                        in = gi[t] < a.n && include_f64(a.x[gi[t]], a.y[gi[t]], a.z[gi[t]], a.x[gj], a.y[gj],
+                                                         a.z[gj], nx, ny, nz, a.L, a.images);
+                    }
+                }
+                if (!in) continue;
+                const float H = hI[t] + RB.z;
+                const float ri = rsqrt_f(r2);
+                const float g = (r2 >= H * H) ? ri * ri * ri : spline_over_r_f(r2 * ri, H);
+                const float sc = B.z * g;
+                px[t] = fmaf(sc, dx, px[t]);
+                py[t] = fmaf(sc, dy, py[t]);
+                pz[t] = fmaf(sc, dz, pz[t]);
+            }
+        }
+#pragma unroll
+        for (int t = 0; t < KI; ++t) {
+            const float p[3] = {px[t], py[t], pz[t]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {  // Kahan fold
+                const float y = p[c] - kc[t][c], tt = kh[t][c] + y;
+                kc[t][c] = (tt - kh[t][c]) - y;
+                kh[t][c] = tt;
+            }
+        }
+    }
+}
+
 template <int KI>
 __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const PeriodicArgs a) {
     constexpr int T = 32 * KI;
@@ -199,80 +269,24 @@ __global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const Periodi
                 const float lx = (float)(dcx - hx), ly = (float)(dcy - hy), lz = (float)(dcz - hz);
                 const bool self_tile = (J == I) && (nx | ny | nz);
                 const bool decide = !((inside >> b) & 1u);
+                // -(s), s = fl(o_i + dc), and -(r_i + remainder(dc) + err(s)), per target
+                float nxs[KI], nys[KI], nzs[KI], nrx[KI], nry[KI], nrz[KI];
 #pragma unroll
                 for (int t = 0; t < KI; ++t) {
-                    // -(s), s = fl(o_i + dc), and -(r_i + remainder(dc) + err(s))
                     float e;
-                    const float nxs = -two_sum_f(xi[t], hx, e);
-                    const float nrx = -((rxi[t] + lx) + e);
-                    const float nys = -two_sum_f(yi[t], hy, e);
-                    const float nry = -((ryi[t] + ly) + e);
-                    const float nzs = -two_sum_f(zi[t], hz, e);
-                    const float nrz = -((rzi[t] + lz) + e);
-                    float hx_ = kh[t][0], hy_ = kh[t][1], hz_ = kh[t][2];
-                    float cx_ = kc[t][0], cy_ = kc[t][1], cz_ = kc[t][2];
-                    for (int f0 = 0; f0 < T; f0 += kFold) {
-                        float px = 0.f, py = 0.f, pz = 0.f;
-                        for (int j = f0; j < f0 + kFold; ++j) {
-                            const float4 A = S[2 * j], B = S[2 * j + 1];
-                            const float4 RA = S[2 * T + 2 * j], RB = S[2 * T + 2 * j + 1];
-                            // d = x_j + nL - x_i
-                            const float dx = (A.x + nxs) + (RA.x + nrx);
-                            const float dy = (A.z + nys) + (RA.z + nry);
-                            const float dz = (B.x + nzs) + (RB.x + nrz);
-                            const float r2 = dx * dx + dy * dy + dz * dz;
-                            if (!(r2 > 0.f) || B.z == 0.f) continue;            // self pair, padding
-                            if (self_tile && j == lane * KI + t) continue;       // j == i: no self images
-                            bool in = true;
-                            bool ambiguous = false;
-                            if (!decide) {
-                                // every pair of this image is a term
-                            } else if (a.images == 1) {
-                                // x_i - x_j - nL = -d in [-L/2, L/2)  <=>  d in (-L/2, L/2]
-                                in = dx > -halfL && dx <= halfL && dy > -halfL && dy <= halfL && dz > -halfL &&
-                                     dz <= halfL;
-                                const float band = kFaceBand * L;
-                                ambiguous = fabsf(fabsf(dx) - halfL) < band || fabsf(fabsf(dy) - halfL) < band ||
-                                            fabsf(fabsf(dz) - halfL) < band;
-                            } else {
-                                in = r2 < cut2;
-                                ambiguous = fabsf(r2 - cut2) < kCutBand * cut2;
-                            }
-                            if (ambiguous && gi[t] >= a.n) ambiguous = false, in = false;  // padding target
-                            if (ambiguous) {
-                                const int64_t gj = J * T + j;
-                                in = include_f64(a.x[gi[t]], a.y[gi[t]], a.z[gi[t]], a.x[gj], a.y[gj], a.z[gj], nx,
-                                                 ny, nz, a.L, a.images);
-                            }
-                            if (!in) continue;
-                            const float H = hI[t] + RB.z;
-                            const float ri = rsqrt_f(r2);
-                            const float g = (r2 >= H * H) ? ri * ri * ri : spline_over_r_f(r2 * ri, H);
-                            const float sc = B.z * g;
-                            px = fmaf(sc, dx, px);
-                            py = fmaf(sc, dy, py);
-                            pz = fmaf(sc, dz, pz);
-                        }
-                        // Kahan fold
-                        float y = px - cx_, tt = hx_ + y;
-                        cx_ = (tt - hx_) - y;
-                        hx_ = tt;
-                        y = py - cy_;
-                        tt = hy_ + y;
-                        cy_ = (tt - hy_) - y;
-                        hy_ = tt;
-                        y = pz - cz_;
-                        tt = hz_ + y;
-                        cz_ = (tt - hz_) - y;
-                        hz_ = tt;
-                    }
-                    kh[t][0] = hx_;
-                    kh[t][1] = hy_;
-                    kh[t][2] = hz_;
-                    kc[t][0] = cx_;
-                    kc[t][1] = cy_;
-                    kc[t][2] = cz_;
+                    nxs[t] = -two_sum_f(xi[t], hx, e);
+                    nrx[t] = -((rxi[t] + lx) + e);
+                    nys[t] = -two_sum_f(yi[t], hy, e);
+                    nry[t] = -((ryi[t] + ly) + e);
+                    nzs[t] = -two_sum_f(zi[t], hz, e);
+                    nrz[t] = -((rzi[t] + lz) + e);
                 }
+                if (decide)
+                    image_terms<KI, T, true>(S, a, nxs, nys, nzs, nrx, nry, nrz, hI, gi, J, nx, ny, nz, self_tile,
+                                             lane, cut2, halfL, L, kh, kc);
+                else
+                    image_terms<KI, T, false>(S, a, nxs, nys, nzs, nrx, nry, nrz, hI, gi, J, nx, ny, nz, self_tile,
+                                              lane, cut2, halfL, L, kh, kc);
             }
         }
 #pragma unroll
