@@ -819,6 +819,108 @@ __global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int
 // are summed in packed FP32x2 on the Newtonian branch; where some lane of the
 // warp meets a pair inside h_i + h_j the full spline of Eq. 4 is taken for
 // that source.  Self pairs (d == 0 exactly) contribute nothing.
+// The terms of one near tile pair for this lane's KI targets (KI/2 packed
+// pairs), folded into the targets' sums every FOLD sources.  Each source is
+// read once from shared memory for all pairs.  SOFT: some pair may lie inside
+// h_i + h_j (or the tile pair is a tile with itself): per source the warp
+// checks and takes the full spline of Eq. 4 where needed, and self pairs
+// (d == 0) add nothing; otherwise every pair is Newtonian and d != 0.
+template <int KI, bool COMP, int FOLD, bool SOFT>
+__device__ __forceinline__ void near_tile_terms(
+    const float4 *__restrict__ S, const float4 *__restrict__ Rr, const float2 (&nxs)[KI / 2],
+    const float2 (&nys)[KI / 2], const float2 (&nzs)[KI / 2], const float2 (&nrx)[KI / 2],
+    const float2 (&nry)[KI / 2], const float2 (&nrz)[KI / 2], const float2 (&hI)[KI / 2], float2 (&hx)[KI / 2],
+    float2 (&hy)[KI / 2], float2 (&hz)[KI / 2], float2 (&cx_)[KI / 2], float2 (&cy_)[KI / 2],
+    float2 (&cz_)[KI / 2]) {
+    constexpr int T = 32 * KI;
+    constexpr int NPAIR = KI / 2;
+#pragma unroll 1
+    for (int f0 = 0; f0 < T; f0 += FOLD) {
+        float2 px[NPAIR], py[NPAIR], pz[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            if (COMP) {
+                px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+            } else {
+                px[q] = hx[q];
+                py[q] = hy[q];
+                pz[q] = hz[q];
+            }
+        }
+#pragma unroll 2
+        for (int j = f0; j < f0 + FOLD; ++j) {
+            const float4 A = S[2 * j], B = S[2 * j + 1];
+            const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxs[q]),
+                                             __fadd2_rn(make_float2(RA.x, RA.y), nrx[q]));
+                const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nys[q]),
+                                             __fadd2_rn(make_float2(RA.z, RA.w), nry[q]));
+                const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzs[q]),
+                                             __fadd2_rn(make_float2(RB.x, RB.y), nrz[q]));
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                if (!SOFT) {
+                    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                    const float2 ri2 = __fmul2_rn(ri, ri);
+                    const float2 sc = __fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ri), ri2);
+                    px[q] = __ffma2_rn(sc, dx, px[q]);
+                    py[q] = __ffma2_rn(sc, dy, py[q]);
+                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
+                    continue;
+                }
+                const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
+                const float2 H2 = __fmul2_rn(H, H);
+                const bool inner = r2.x < H2.x || r2.y < H2.y;
+                if (!__any_sync(0xffffffffu, inner)) {
+                    const float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
+                                                  r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
+                    const float2 ri2 = __fmul2_rn(ri, ri);
+                    float2 sc = __fmul2_rn(make_float2(B.z, B.w), ri);
+                    sc = __fmul2_rn(sc, ri2);
+                    px[q] = __ffma2_rn(sc, dx, px[q]);
+                    py[q] = __ffma2_rn(sc, dy, py[q]);
+                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
+                } else {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float r2e = e ? r2.y : r2.x;
+                        if (r2e > 0.f) {
+                            const float He = e ? H.y : H.x;
+                            const float ri = rsqrt_approx(r2e);
+                            const float g = (r2e >= He * He) ? ri * ri * ri : spline_over_r_f32(r2e * ri, He);
+                            const float sc = B.z * g;
+                            if (e) {
+                                px[q].y = fmaf(sc, dx.y, px[q].y);
+                                py[q].y = fmaf(sc, dy.y, py[q].y);
+                                pz[q].y = fmaf(sc, dz.y, pz[q].y);
+                            } else {
+                                px[q].x = fmaf(sc, dx.x, px[q].x);
+                                py[q].x = fmaf(sc, dy.x, py[q].x);
+                                pz[q].x = fmaf(sc, dz.x, pz[q].x);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            if (COMP) {
+                kahan2(hx[q], cx_[q], px[q]);
+                kahan2(hy[q], cy_[q], py[q]);
+                kahan2(hz[q], cz_[q], pz[q]);
+            } else {
+                hx[q] = px[q];
+                hy[q] = py[q];
+                hz[q] = pz[q];
+            }
+        }
+    }
+}
+
 template <int KI, bool COMP, int FOLD>
 __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
@@ -917,91 +1019,40 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
             const float dcx = two_diff(ci.x, cj.x, edx);
             const float dcy = two_diff(ci.y, cj.y, edy);
             const float dcz = two_diff(ci.z, cj.z, edz);
+            // -(xs), xs = fl(o_i + dc), and -(r_i + err(dc) + err(xs)), per target pair
+            float2 nxs[NPAIR], nys[NPAIR], nzs[NPAIR], nrx[NPAIR], nry[NPAIR], nrz[NPAIR];
 #pragma unroll
             for (int q = 0; q < NPAIR; ++q) {
-                // -(xs), xs = fl(o_i + dc), and -(r_i + err(dc) + err(xs)) for both targets
-                float2 nxs, nys, nzs, nrx, nry, nrz;
-                {
-                    float e0, e1;
-                    nxs.x = -two_sum(xi[q].x, dcx, e0);
-                    nxs.y = -two_sum(xi[q].y, dcx, e1);
-                    nrx = make_float2(-((rxi[q].x + edx) + e0), -((rxi[q].y + edx) + e1));
-                    nys.x = -two_sum(yi[q].x, dcy, e0);
-                    nys.y = -two_sum(yi[q].y, dcy, e1);
-                    nry = make_float2(-((ryi[q].x + edy) + e0), -((ryi[q].y + edy) + e1));
-                    nzs.x = -two_sum(zi[q].x, dcz, e0);
-                    nzs.y = -two_sum(zi[q].y, dcz, e1);
-                    nrz = make_float2(-((rzi[q].x + edz) + e0), -((rzi[q].y + edz) + e1));
-                }
-#pragma unroll 1
-                for (int f0 = 0; f0 < T; f0 += FOLD) {
-                    float2 px, py, pz;
-                    if (COMP) {
-                        px = py = pz = make_float2(0.f, 0.f);
-                    } else {
-                        px = hx[q];
-                        py = hy[q];
-                        pz = hz[q];
-                    }
-#pragma unroll 2
-                    for (int j = f0; j < f0 + FOLD; ++j) {
-                        const float4 A = S[2 * j], B = S[2 * j + 1];
-                        const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
-                        const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxs),
-                                                     __fadd2_rn(make_float2(RA.x, RA.y), nrx));
-                        const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nys),
-                                                     __fadd2_rn(make_float2(RA.z, RA.w), nry));
-                        const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzs),
-                                                     __fadd2_rn(make_float2(RB.x, RB.y), nrz));
-                        float2 r2 = __fmul2_rn(dx, dx);
-                        r2 = __ffma2_rn(dy, dy, r2);
-                        r2 = __ffma2_rn(dz, dz, r2);
-                        const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
-                        const float2 H2 = __fmul2_rn(H, H);
-                        const bool inner = r2.x < H2.x || r2.y < H2.y;
-                        if (!__any_sync(0xffffffffu, inner)) {
-                            const float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
-                                                          r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
-                            const float2 ri2 = __fmul2_rn(ri, ri);
-                            float2 sc = __fmul2_rn(make_float2(B.z, B.w), ri);
-                            sc = __fmul2_rn(sc, ri2);
-                            px = __ffma2_rn(sc, dx, px);
-                            py = __ffma2_rn(sc, dy, py);
-                            pz = __ffma2_rn(sc, dz, pz);
-                        } else {
-#pragma unroll
-                            for (int e = 0; e < 2; ++e) {
-                                const float r2e = e ? r2.y : r2.x;
-                                if (r2e > 0.f) {
-                                    const float He = e ? H.y : H.x;
-                                    const float ri = rsqrt_approx(r2e);
-                                    const float g = (r2e >= He * He) ? ri * ri * ri
-                                                                     : spline_over_r_f32(r2e * ri, He);
-                                    const float sc = B.z * g;
-                                    if (e) {
-                                        px.y = fmaf(sc, dx.y, px.y);
-                                        py.y = fmaf(sc, dy.y, py.y);
-                                        pz.y = fmaf(sc, dz.y, pz.y);
-                                    } else {
-                                        px.x = fmaf(sc, dx.x, px.x);
-                                        py.x = fmaf(sc, dy.x, py.x);
-                                        pz.x = fmaf(sc, dz.x, pz.x);
-                                    }
-                                }
-                            }
-                        }
-                    }
-                    if (COMP) {
-                        kahan2(hx[q], cx_[q], px);
-                        kahan2(hy[q], cy_[q], py);
-                        kahan2(hz[q], cz_[q], pz);
-                    } else {
-                        hx[q] = px;
-                        hy[q] = py;
-                        hz[q] = pz;
-                    }
-                }
+                float e0, e1;
+                nxs[q].x = -two_sum(xi[q].x, dcx, e0);
+                nxs[q].y = -two_sum(xi[q].y, dcx, e1);
+                nrx[q] = make_float2(-((rxi[q].x + edx) + e0), -((rxi[q].y + edx) + e1));
+                nys[q].x = -two_sum(yi[q].x, dcy, e0);
+                nys[q].y = -two_sum(yi[q].y, dcy, e1);
+                nry[q] = make_float2(-((ryi[q].x + edy) + e0), -((ryi[q].y + edy) + e1));
+                nzs[q].x = -two_sum(zi[q].x, dcz, e0);
+                nzs[q].y = -two_sum(zi[q].y, dcz, e1);
+                nrz[q] = make_float2(-((rzi[q].x + edz) + e0), -((rzi[q].y + edz) + e1));
             }
+            // Can any pair of the two tiles lie inside h_i + h_j?  (the softening test of
+            // tile_pair_near; the tile itself always can, it holds the self pairs)
+            const float4 ej = a.tbox_e[d.tile_off + jt];
+            bool soft = d.tile_off + jt == itile;
+            {
+                const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
+                const float gx = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcx), dn), __fmul_rn(__fadd_rn(ei.x, ej.x), up)));
+                const float gy = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcy), dn), __fmul_rn(__fadd_rn(ei.y, ej.y), up)));
+                const float gz = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcz), dn), __fmul_rn(__fadd_rn(ei.z, ej.z), up)));
+                const float gap2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+                const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
+                soft = soft || gap2 <= __fmul_rn(hs, hs);
+            }
+            if (soft)
+                near_tile_terms<KI, COMP, FOLD, true>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
+                                                      cz_);
+            else
+                near_tile_terms<KI, COMP, FOLD, false>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
+                                                       cz_);
             __syncwarp();  // every lane is done with buffer b before it is refilled
             jt = jn;
             b ^= 1;
