@@ -38,6 +38,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "pair_terms.cuh"
 #include "steps_internal.h"
 
 namespace steps {
@@ -102,68 +103,6 @@ __device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t
             dst),
         "l"(src), "r"(bytes), "r"(bar)
         : "memory");
-}
-
-// MUFU reciprocal square root (approximate, flush-to-zero).
-__device__ __forceinline__ float rsqrt_approx(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Fcal(r, H)/r of Eq. 4 for r < H (u = r/H), in FP32.  The second branch is
-// rewritten around v = 1 - u so that its polynomial has only positive terms
-// (16/15 + 16/5 v + 32/5 v^2 + 32/3 v^3, algebraically identical to the printed
-// form) and does not cancel near u = 1.
-__device__ __forceinline__ float spline_over_r_f32(float r, float H) {
-    const float Hinv = __frcp_rn(H);
-    const float u = r * Hinv;
-    const float Hinv3 = Hinv * Hinv * Hinv;
-    float g;
-    if (u < 0.5f) {
-        g = 32.0f / 3.0f + u * u * (32.0f * u - 38.4f);
-    } else {
-        const float v = 1.0f - u;
-        const float P = 16.0f / 15.0f + v * (3.2f + v * (6.4f + v * (32.0f / 3.0f)));
-        g = P - __frcp_rn(15.0f * u * u * u);
-    }
-    return g * Hinv3;
-}
-
-// Error-free difference: a - b = s + e exactly (Knuth's TwoSum on a + (-b)).
-__device__ __forceinline__ float two_diff(float a, float b, float &e) {
-    const float s = __fsub_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fsub_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fadd_rn(b, bb));
-    return s;
-}
-
-// Error-free sum: a + b = s + e exactly.
-__device__ __forceinline__ float two_sum(float a, float b, float &e) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return s;
-}
-
-// Packed Kahan step for two targets at once: (hi, -c) absorbs p.
-//   y = p - c;  t = hi + y;  c' = (t - hi) - y;  hi = t
-// with nc = -c kept negated so that every step is one packed add or FMA.
-__device__ __forceinline__ void kahan2(float2 &hi, float2 &nc, const float2 p) {
-    const float2 neg1 = make_float2(-1.0f, -1.0f);
-    const float2 y = __fadd2_rn(p, nc);
-    const float2 t = __fadd2_rn(hi, y);
-    const float2 u = __ffma2_rn(hi, neg1, t);  // t - hi
-    nc = __ffma2_rn(u, neg1, y);               // y - (t - hi) = -c'
-    hi = t;
-}
-
-// Scalar Kahan step, same convention as kahan2 (nc holds the negated compensation).
-__device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
-    const float y = __fadd_rn(p, nc);
-    const float t = __fadd_rn(hi, y);
-    nc = __fsub_rn(y, __fsub_rn(t, hi));
-    hi = t;
 }
 
 // Tile-pair classification (done once per pair by the far-field producer;
@@ -819,108 +758,6 @@ __global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int
 // are summed in packed FP32x2 on the Newtonian branch; where some lane of the
 // warp meets a pair inside h_i + h_j the full spline of Eq. 4 is taken for
 // that source.  Self pairs (d == 0 exactly) contribute nothing.
-// The terms of one near tile pair for this lane's KI targets (KI/2 packed
-// pairs), folded into the targets' sums every FOLD sources.  Each source is
-// read once from shared memory for all pairs.  SOFT: some pair may lie inside
-// h_i + h_j (or the tile pair is a tile with itself): per source the warp
-// checks and takes the full spline of Eq. 4 where needed, and self pairs
-// (d == 0) add nothing; otherwise every pair is Newtonian and d != 0.
-template <int KI, bool COMP, int FOLD, bool SOFT>
-__device__ __forceinline__ void near_tile_terms(
-    const float4 *__restrict__ S, const float4 *__restrict__ Rr, const float2 (&nxs)[KI / 2],
-    const float2 (&nys)[KI / 2], const float2 (&nzs)[KI / 2], const float2 (&nrx)[KI / 2],
-    const float2 (&nry)[KI / 2], const float2 (&nrz)[KI / 2], const float2 (&hI)[KI / 2], float2 (&hx)[KI / 2],
-    float2 (&hy)[KI / 2], float2 (&hz)[KI / 2], float2 (&cx_)[KI / 2], float2 (&cy_)[KI / 2],
-    float2 (&cz_)[KI / 2]) {
-    constexpr int T = 32 * KI;
-    constexpr int NPAIR = KI / 2;
-#pragma unroll 1
-    for (int f0 = 0; f0 < T; f0 += FOLD) {
-        float2 px[NPAIR], py[NPAIR], pz[NPAIR];
-#pragma unroll
-        for (int q = 0; q < NPAIR; ++q) {
-            if (COMP) {
-                px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
-            } else {
-                px[q] = hx[q];
-                py[q] = hy[q];
-                pz[q] = hz[q];
-            }
-        }
-#pragma unroll 2
-        for (int j = f0; j < f0 + FOLD; ++j) {
-            const float4 A = S[2 * j], B = S[2 * j + 1];
-            const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
-#pragma unroll
-            for (int q = 0; q < NPAIR; ++q) {
-                const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxs[q]),
-                                             __fadd2_rn(make_float2(RA.x, RA.y), nrx[q]));
-                const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nys[q]),
-                                             __fadd2_rn(make_float2(RA.z, RA.w), nry[q]));
-                const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzs[q]),
-                                             __fadd2_rn(make_float2(RB.x, RB.y), nrz[q]));
-                float2 r2 = __fmul2_rn(dx, dx);
-                r2 = __ffma2_rn(dy, dy, r2);
-                r2 = __ffma2_rn(dz, dz, r2);
-                if (!SOFT) {
-                    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                    const float2 ri2 = __fmul2_rn(ri, ri);
-                    const float2 sc = __fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ri), ri2);
-                    px[q] = __ffma2_rn(sc, dx, px[q]);
-                    py[q] = __ffma2_rn(sc, dy, py[q]);
-                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
-                    continue;
-                }
-                const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
-                const float2 H2 = __fmul2_rn(H, H);
-                const bool inner = r2.x < H2.x || r2.y < H2.y;
-                if (!__any_sync(0xffffffffu, inner)) {
-                    const float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
-                                                  r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
-                    const float2 ri2 = __fmul2_rn(ri, ri);
-                    float2 sc = __fmul2_rn(make_float2(B.z, B.w), ri);
-                    sc = __fmul2_rn(sc, ri2);
-                    px[q] = __ffma2_rn(sc, dx, px[q]);
-                    py[q] = __ffma2_rn(sc, dy, py[q]);
-                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 2; ++e) {
-                        const float r2e = e ? r2.y : r2.x;
-                        if (r2e > 0.f) {
-                            const float He = e ? H.y : H.x;
-                            const float ri = rsqrt_approx(r2e);
-                            const float g = (r2e >= He * He) ? ri * ri * ri : spline_over_r_f32(r2e * ri, He);
-                            const float sc = B.z * g;
-                            if (e) {
-                                px[q].y = fmaf(sc, dx.y, px[q].y);
-                                py[q].y = fmaf(sc, dy.y, py[q].y);
-                                pz[q].y = fmaf(sc, dz.y, pz[q].y);
-                            } else {
-                                px[q].x = fmaf(sc, dx.x, px[q].x);
-                                py[q].x = fmaf(sc, dy.x, py[q].x);
-                                pz[q].x = fmaf(sc, dz.x, pz[q].x);
-                            }
-                        }
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int q = 0; q < NPAIR; ++q) {
-            if (COMP) {
-                kahan2(hx[q], cx_[q], px[q]);
-                kahan2(hy[q], cy_[q], py[q]);
-                kahan2(hz[q], cz_[q], pz[q]);
-            } else {
-                hx[q] = px[q];
-                hy[q] = py[q];
-                hz[q] = pz[q];
-            }
-        }
-    }
-}
-
 template <int KI, bool COMP, int FOLD>
 __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
