@@ -121,6 +121,21 @@ def dist_env():
     return ws, rank, local
 
 
+def job_throughput(local_seconds: float, units_per_rank: float, device=None):
+    """Whole-job value of independent replicas: the units every rank processed
+    over the slowest rank's time (max over ranks); (value, seconds).  A single
+    process (no process group) is its own job."""
+    import torch
+    import torch.distributed as dist
+    ws = dist.get_world_size() if dist.is_available() and dist.is_initialized() else 1
+    seconds = float(local_seconds)
+    if ws > 1:
+        t = torch.tensor([seconds], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        seconds = float(t.item())
+    return units_per_rank * ws / seconds, seconds
+
+
 def build_workload(name: str):
     from paper_1811_05903_gb300 import workloads
     if name == "precision_1m":
@@ -344,13 +359,7 @@ def run_ours(args):
     force_ms, force_launches, kernel_launches = steps.steps_profile_read(sim.ctx, reset=True)
     near_pairs, all_pairs = steps.steps_force_stats(sim.ctx)
     steps.steps_profile_enable(sim.ctx, False)
-    total_s = sum(step_ms) * 1e-3
-    if ws > 1:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_s = float(t.item())
-    interactions = args.steps * n * n * ws
-    value = interactions / total_s
+    value, total_s = job_throughput(sum(step_ms) * 1e-3, args.steps * n * n, device=dev)
 
     # ---- end to end through the C ABI with host buffers ----
     pos_h = torch.empty((n, 3), dtype=torch.float64).pin_memory()
