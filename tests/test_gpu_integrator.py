@@ -178,3 +178,32 @@ def test_invalid_inputs_rejected(what):
     with pytest.raises(steps.StepsError) as e:
         steps.Simulation(pos, vel, m, soft=soft, h_min=p.h_min)
     assert e.value.status == steps.STEPS_EINVAL
+
+
+def test_config2_full_run_forces_stay_within_contract():
+    """The StePS-like compactified LCDM run of N = 262,144 (131,072 central
+    particles + 64 shells x 2,048) taken through all 200 log-a KDK steps from
+    a = 0.02 to a = 1 in the graph-replayed loop.  Trajectories are chaotic, so
+    the run is checked where the oracle can follow it one target at a time: the
+    scale factor reaches 1 (RK4 against the closed form), the state stays
+    finite, and the mixed-precision pair term on 512 seeded targets of the
+    evolved, clustered state meets the same contract as on the initial state."""
+    import time
+    p = workloads.lcdm_262k()
+    a_sched, dts = workloads.loga_schedule(p.a0, 1.0, 200, p.Om, p.OL)
+    sim = make_sim(p)
+    t0 = time.perf_counter()
+    sim.run(dts)
+    pos, vel, acc, t, a = sim.state()
+    secs = time.perf_counter() - t0
+    sim.close()
+    print("262,144 particles, 200 steps: %.2f s, %.3e interactions/s" % (secs, 200 * p.n ** 2 / secs))
+    assert abs(a - 1.0) <= 1e-9
+    assert np.isfinite(pos).all() and np.isfinite(vel).all() and np.isfinite(acc).all()
+    h = oracle.softening(p.mass, p.h_min)
+    tg = np.sort(np.random.default_rng(2002).choice(p.n, 512, replace=False))
+    ref = oracle.pair_acc(pos, p.mass, h, p.G, targets=tg)
+    e = np.linalg.norm(acc[tg] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+    rms = np.sqrt(np.mean(e ** 2))
+    print("evolved state: rms %.2e max %.2e" % (rms, e.max()))
+    assert rms <= 1e-6 and e.max() <= 2e-5, (rms, e.max())
