@@ -410,9 +410,13 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->err, 2));
     c->flag = c->err + 1;
     STEPS_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->st));
-    // staging: padded so that every variant's i-block (W x 32 KI targets, all
-    // dividing 6144) fits; each variant pads to its own multiple
-    c->np = (n + 6143) / 6144 * 6144;
+    // staging: padded to the largest multiple any variant's i-block (W x 32 KI
+    // targets) needs, so that every variant fits; each pads to its own multiple
+    c->np = 0;
+    for (int k = 0; k < num_variants(); ++k) {
+        const int64_t bi = (int64_t)variant(k).W * 32 * variant(k).KI;
+        c->np = std::max<int64_t>(c->np, (n + bi - 1) / bi * bi);
+    }
     c->ntile_cap = c->np / 64;
     STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->rdup_buf, 2 * c->np));
