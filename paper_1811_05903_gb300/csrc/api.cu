@@ -172,8 +172,10 @@ steps_status sync_and_check(steps_ctx *c) {
     return STEPS_OK;
 }
 
-// Default variant before tuning: 4 targets per thread, 4 compute warps; small
-// systems use 64-particle tiles (2 targets per thread) to limit padding.
+// Default variant before tuning (and the choice below 2^17 particles): the
+// first built variant of the requested summation mode with 4 targets per
+// thread; systems below 32,768 particles use 64-particle tiles (2 targets per
+// thread) to limit padding and near-field work.
 int pick_variant(const steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
     if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())

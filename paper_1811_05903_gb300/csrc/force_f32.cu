@@ -16,18 +16,22 @@
 //    grid: every CTA gets the same number of tile pairs; per-CTA partial sums
 //    per i-block are combined in a fixed order by the fixup kernel, so results
 //    are deterministic and there are no atomics on the sums.
-//  * A producer warp streams j tiles (32 B/particle duplicated layout + 4 B
-//    softening) into an NS-stage shared-memory ring with cp.async.bulk
-//    (TMA bulk copies) completing on mbarriers.
+//  * A producer warp streams j tiles into an NS-stage shared-memory ring with
+//    cp.async.bulk (TMA bulk copies) completing on mbarriers, and classifies
+//    every tile pair: far pairs (provably Newtonian, r >= h_i + h_j, and far
+//    enough for the FP32 arithmetic below) stay in this kernel; near pairs
+//    (neighbours, self pairs, pairs that may lie inside the softening) are
+//    marked in a bitmap and summed by the near-field kernel with exact
+//    separations and the full spline of Eq. 4.
 //  * Compute warps hold KI targets per thread as KI/2 packed pairs and use
-//    Blackwell's packed FP32x2 FMA/ADD/MUL (FFMA2): 12 FP32 lane operations
-//    + 1 MUFU rsqrt per interaction.  Each j element is one pair of
-//    broadcast shared-memory loads.
-//  * Tile pairs whose boxes are provably farther apart than the largest
-//    h_i + h_j take a warp-uniform Newtonian fast path; the rest (neighbouring
-//    tiles, self pairs) take the full spline path of Eq. 4.
+//    Blackwell's packed FP32x2 FMA/ADD/MUL (FFMA2).  Explicit form: 12 FP32
+//    lane operations + 1 MUFU rsqrt per interaction from a 32-byte-per-source
+//    duplicated layout.  Expansion form (the tuned default): |o_j - s|^2
+//    expanded about the source tile's centre with the mass folded in, 10 lane
+//    operations + 1 MUFU from a 64-byte layout.  Each source is a few
+//    broadcast shared-memory loads shared by all of a thread's target pairs.
 //  * STEPS_F32_COMP: per-tile FP32 partial sums are folded into a per-target
-//    (hi, lo) pair with TwoSum (compensated summation), O(N/T) per target.
+//    (hi, lo) pair with TwoSum (compensated summation) every FOLD sources.
 //    STEPS_F32_NAIVE: a single FP32 running sum per target.
 //  * Every mbarrier wait is bounded by a %globaltimer deadline; a wait that
 //    runs out records STEPS_ETIMEOUT, the producer drains its own copies and
