@@ -89,6 +89,7 @@ struct steps_ctx {
     Staging stg;
     float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *fdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
     NearScratch nr;                       // near-field bitmap and work items
+    double *per_part = nullptr;           // periodic mode: FP64 partials per work item
     SimDesc *dsim = nullptr;              // device table of one system
     unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
     float alpha = 0.03125f;
@@ -202,7 +203,7 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.ntile = c->stg.np / c->stg.T;
     c->stg.jdup = c->jdup_buf;
     c->stg.rdup = c->rdup_buf;
-    c->stg.fdup = v.form == 1 ? c->fdup_buf : nullptr;
+    c->stg.fdup = (v.form == 1 || c->cosmo.periodic) ? c->fdup_buf : nullptr;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     SimDesc d{};
@@ -269,7 +270,7 @@ steps_status compute_forces(steps_ctx *c) {
             STEPS_CUDA(cudaGetLastError());
             if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
             STEPS_CUDA(launch_periodic_f32(c->stg, c->x, c->y, c->z, c->cosmo.box, c->cfg.images, c->cosmo.G,
-                                           c->nr.item_part, c->ax, c->ay, c->az, c->st));
+                                           c->per_part, c->num_sms, c->ax, c->ay, c->az, c->st));
             c->kernel_launches += 3;  // stage, periodic, reduce
         }
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
@@ -431,6 +432,8 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     // near-field work-item partials: up to 8 items per target tile (the chunk
     // size adapts on the device), 3 doubles per particle per item
     STEPS_TRY(alloc_n(c, &c->nr.item_part, (size_t)24 * c->np));
+    if (c->cosmo.periodic && c->cfg.prec != STEPS_F64)
+        STEPS_TRY(alloc_n(c, &c->per_part, periodic_part_elems(c->np, c->num_sms)));
     STEPS_TRY(alloc_n(c, &c->stats, 2));
     STEPS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st));
     STEPS_TRY(alloc_n(c, &c->tbc_buf, c->ntile_cap));

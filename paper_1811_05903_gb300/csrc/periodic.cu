@@ -5,77 +5,62 @@
 // x_i - x_j - nL in [-L/2, L/2)^3, n = floor((x_i - x_j) / L + 1/2) per component.
 //
 // FP32 path.  Positions are the FP32 tile staging of the open-boundary path
-// (offset o and residual r from an FP32 tile centre c).  For a target tile I,
-// a source tile J and an image n, the shift c_I - (c_J + nL) is formed in FP64
-// and split into an FP32 value and its FP32 remainder; the pair separation is
-// then carried to ~1 ulp of its own size as in the near-field kernel (exact
-// rounding errors of the shifted target, both offset residuals).  Whether a
-// (pair, image) term belongs to the sum is a hard decision: it is taken on the
-// FP32 separation, except within a thin band around the cut sphere (or the
-// half-box faces) where it is re-taken in FP64 from the FP64 positions with the
-// definition's own expression, so that it matches an FP64 evaluation of the
-// definition; images whose whole tile box lies inside the cut sphere (or inside
-// the half-box region) skip the per-pair decision.  Each warp owns one target
-// tile and a chunk of source tiles (a work item); FP32 partial sums are
-// Kahan-folded every 8 sources across all images of a source tile and then
-// added into FP64 per-target sums, written per work item and added in item
-// order by the reduction kernel: deterministic.
+// (offset o and residual r from an FP32 tile centre c, plus the far-field
+// expansion layout).  For a target tile I, a source tile J and an image n the
+// shift D = c_I - (c_J + nL) is formed in FP64 and split into an FP32 value and
+// its FP32 remainder (per axis: seven values of n per tile pair).  FP32 box
+// tests with conservative margins sort the images of a tile pair into
+//  * far, wholly inside the cut sphere (or the half-box region): every pair is
+//    a Newtonian term; summed by expansion about the source tile's centre
+//    with packed FP32x2 arithmetic (10 lane operations + 1 MUFU per term), the
+//    target shift's rounding undone with the tile's monopole tidal tensor;
+//  * far, straddling the cut sphere: the same, and each term is kept when
+//    k_j r^2 < k_j (2.6 L)^2; terms within a thin band of the cut are decided
+//    again in FP64 from the FP64 positions with the definition's expression;
+//  * near (some pair may lie inside h_i + h_j, or the tile pair is too close
+//    for the expansion, or I = J): exact separations to ~1 ulp of their own
+//    size, the full spline of Eq. 4, and per-pair FP64 re-decisions in the
+//    thin bands around the cut sphere or the half-box faces.
+// Each warp owns one target tile and a chunk of source tiles (a work item);
+// lanes are grouped into image slots so that one warp runs 32 / (T / KF)
+// images at once with KF targets per lane and the source loads are shared
+// (broadcast) by all slots.  FP32 partial sums are Kahan-folded every 32 (far)
+// or 8 (near) sources, added into FP64 per source tile, combined across the
+// slots in a fixed order and written per work item; the reduction kernel adds
+// the items in order: deterministic.
 //
 // FP64 path.  One thread per target, every source, the image loops of the
 // definition in FP64 without contraction (the comparison variant).
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
+
+#include "pair_terms.cuh"
 #include "steps_internal.h"
 
 namespace steps {
 namespace {
 
-constexpr int kWarps = 4;
-constexpr int kFold = 8;
-constexpr float kCutBand = 4e-6f;  // relative band around (2.6 L)^2 decided in FP64
-constexpr float kFaceBand = 2e-6f; // band around +-L/2 (in units of L) decided in FP64
+constexpr int kWarps = 4;            // independent work items (warps) per CTA
+constexpr int kFoldFar = 32;         // sources per FP32 partial before a Kahan fold (far images)
+constexpr int kFoldExact = 8;        // the same on the exact (near) path
+constexpr float kCutBand = 4e-6f;    // relative band around (2.6 L)^2 decided in FP64
+constexpr float kFaceBand = 2e-6f;   // band around +-L/2 (in units of L) decided in FP64
+constexpr float kAlpha2 = 0.03125f * 0.03125f;  // expansion needs gap >= alpha (distance + extents)
+constexpr int kListCap = 344;        // >= 343 candidate images
+constexpr uint16_t kAllIn = 0x200;   // list flag: every pair of the image is a term
 
-__device__ __forceinline__ float two_sum_f(float a, float b, float &e) {
-    const float s = __fadd_rn(a, b);
-    const float bb = __fsub_rn(s, a);
-    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-    return s;
-}
-
-__device__ __forceinline__ float rsqrt_f(float x) {
-    float y;
-    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-    return y;
-}
-
-// Fcal(r, H)/r of Eq. 4 for r < H (FP32; second branch arranged around v = 1 - u).
-__device__ __forceinline__ float spline_over_r_f(float r, float H) {
-    const float Hinv = __frcp_rn(H);
-    const float u = r * Hinv;
-    const float Hinv3 = Hinv * Hinv * Hinv;
-    float g;
-    if (u < 0.5f) {
-        g = 32.0f / 3.0f + u * u * (32.0f * u - 38.4f);
-    } else {
-        const float v = 1.0f - u;
-        g = 16.0f / 15.0f + v * (3.2f + v * (6.4f + v * (32.0f / 3.0f))) - __frcp_rn(15.0f * u * u * u);
-    }
-    return g * Hinv3;
-}
-
-__device__ __forceinline__ double spline_over_r_d(double r, double H) {
-    const double Hinv = 1.0 / H;
-    const double u = r * Hinv;
-    double g;
-    if (u < 0.5) {
-        g = 32.0 / 3.0 + u * u * (32.0 * u - 38.4);
-    } else {
-        const double v = 1.0 - u;
-        g = 16.0 / 15.0 + v * (3.2 + v * (6.4 + v * (32.0 / 3.0))) - 1.0 / (15.0 * u * u * u);
-    }
-    return g * Hinv * Hinv * Hinv;
-}
+// Per-warp shared memory.
+template <int T, int KF>
+struct WarpSmem {
+    float4 sf[4 * T];          // tile J in the far-field expansion layout
+    float4 sk[T];              // per source: (-k c2, -k c2, band k c2, band k c2), c2 = (2.6 L)^2
+    double acc[3 * KF][32];    // FP64 sums of this lane's targets, [component * KF + target][lane]
+    float tx[T], ty[T], tz[T]; // tile I: target offsets
+    float dh[24], dl[24];      // [axis * 7 + n + 3]: FP32 value and remainder of c_I - (c_J + nL)
+    uint16_t lf[kListCap], lc[kListCap], le[kListCap];  // far-inside, far-straddling, near images
+};
 
 // Image k of the candidate table: cut sum |n_c| <= 3 (7^3 entries; a term needs
 // |n_c| L < 2.6 L + |x_i - x_j|_c < 3.6 L), quasi-periodic |n_c| <= 1 (27).
@@ -89,6 +74,19 @@ __device__ __forceinline__ void image_of(int k, int images, int &nx, int &ny, in
         ny = (k / 7) % 7 - 3;
         nz = k % 7 - 3;
     }
+}
+
+__device__ __forceinline__ double spline_over_r_d(double r, double H) {
+    const double Hinv = 1.0 / H;
+    const double u = r * Hinv;
+    double g;
+    if (u < 0.5) {
+        g = 32.0 / 3.0 + u * u * (32.0 * u - 38.4);
+    } else {
+        const double v = 1.0 - u;
+        g = 16.0 / 15.0 + v * (3.2 + v * (6.4 + v * (32.0 / 3.0))) - 1.0 / (15.0 * u * u * u);
+    }
+    return g * Hinv * Hinv * Hinv;
 }
 
 // The definition's decision in FP64, with the oracle's expression (no contraction).
@@ -108,38 +106,202 @@ __device__ __noinline__ bool include_f64(double xi, double yi, double zi, double
     return r2 < __dmul_rn(cut, cut);
 }
 
-// The terms of one (source tile, image) for this lane's KI targets, added to
-// the targets' compensated sums (folded every kFold sources).  Each source is
-// read once from shared memory and used for all KI targets.  DECIDE: some
-// pairs of this image may fall outside the cut sphere (or the half-box
-// region), so every term is tested; otherwise every pair is a term.
-template <int KI, int T, bool DECIDE>
-__device__ __forceinline__ void image_terms(const float4 *__restrict__ S, const PeriodicArgs &a,
-                                            const float (&nxs)[KI], const float (&nys)[KI], const float (&nzs)[KI],
-                                            const float (&nrx)[KI], const float (&nry)[KI], const float (&nrz)[KI],
-                                            const float (&hI)[KI], const int64_t (&gi)[KI], int64_t J, int nx,
-                                            int ny, int nz, bool self_tile, int lane, float cut2, float halfL,
-                                            float L, float (&kh)[KI][3], float (&kc)[KI][3]) {
-    for (int f0 = 0; f0 < T; f0 += kFold) {
-        float px[KI], py[KI], pz[KI];
+// What the per-term FP64 decisions need (sorted FP64 positions and indices).
+struct DecideCtx {
+    const double *x, *y, *z;
+    int64_t n;
+    double L;
+    int images;
+    int nx, ny, nz;  // the image
+    int64_t gi0;     // global index of this lane's first target
+    int64_t gj0;     // global index of the source tile's first particle
+};
+
+// Terms of a straddling far image within the FP32 band of the cut: the
+// definition's FP64 decision for each of the two packed targets (2 q, 2 q + 1).
+__device__ __noinline__ float2 cut_decide(float2 sc, const float2 dt, const float band, const DecideCtx dc,
+                                          const int t0, const int j) {
+    const int64_t gj = dc.gj0 + j;
 #pragma unroll
-        for (int t = 0; t < KI; ++t) px[t] = py[t] = pz[t] = 0.f;
+    for (int e = 0; e < 2; ++e) {
+        const float d = e ? dt.y : dt.x;
+        const int64_t gi = dc.gi0 + t0 + e;
+        bool in;
+        if (fabsf(d) < band)
+            in = gi < dc.n && gj < dc.n &&
+                 include_f64(dc.x[gi], dc.y[gi], dc.z[gi], dc.x[gj], dc.y[gj], dc.z[gj], dc.nx, dc.ny, dc.nz, dc.L,
+                             0);
+        else
+            in = d < 0.f;
+        if (!in) {
+            if (e)
+                sc.y = 0.f;
+            else
+                sc.x = 0.f;
+        }
+    }
+    return sc;
+}
+
+// The terms of one far image (source tile J shifted by nL) for this lane's KF
+// targets, every pair Newtonian.  With s = fl(o_i + D) the target relative to
+// the shifted source tile's centre, n = -s and k_j = m_j^(-2/3) rounded to FP32,
+//     k_j |o_j - s|^2 = k_j |n|^2 + k_j |o_j|^2 + (2 k_j o_j) . n
+// (a four-step FMA chain on the staged coefficients), and
+// (k_j |o_j - s|^2)^(-3/2) = m_j / |x_j + nL - x_i|^3.  The rounding of the
+// target shift, l = (o_i + D) - s, is the same for every source of the tile; it
+// is undone to first order with the tile's monopole tidal tensor,
+// p += M (3 n (n.l) / R^5 - l / R^3).  CUT: the image straddles the cut
+// sphere; a term counts when k_j r^2 < k_j (2.6 L)^2, and terms within a
+// relative band of 4e-6 of the cut are decided in FP64 (cut_decide).
+template <int T, int NPAIR, bool CUT>
+__device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const float (&D)[6], const float M,
+                                          const int ti0, const bool act, const DecideCtx &dc,
+                                          float2 (&hx)[NPAIR], float2 (&hy)[NPAIR], float2 (&hz)[NPAIR],
+                                          float2 (&cx)[NPAIR], float2 (&cy)[NPAIR], float2 (&cz)[NPAIR]) {
+    const float2 neg1 = make_float2(-1.f, -1.f);
+    float2 nx[NPAIR], ny[NPAIR], nz[NPAIR], ss[NPAIR];
+    float2 px[NPAIR], py[NPAIR], pz[NPAIR];  // sum of w^3 o_j (starts at the shift correction)
+    {
+        const float2 dhx = make_float2(D[0], D[0]), dhy = make_float2(D[1], D[1]), dhz = make_float2(D[2], D[2]);
+        const float2 dlx = make_float2(D[3], D[3]), dly = make_float2(D[4], D[4]), dlz = make_float2(D[5], D[5]);
+        const float2 ndx = make_float2(-D[0], -D[0]), ndy = make_float2(-D[1], -D[1]),
+                     ndz = make_float2(-D[2], -D[2]);
+        const float2 M2 = make_float2(M, M);
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            const float2 xi = *reinterpret_cast<const float2 *>(&W.tx[ti0 + 2 * q]);
+            const float2 yi = *reinterpret_cast<const float2 *>(&W.ty[ti0 + 2 * q]);
+            const float2 zi = *reinterpret_cast<const float2 *>(&W.tz[ti0 + 2 * q]);
+            nx[q] = __ffma2_rn(xi, neg1, ndx);
+            ny[q] = __ffma2_rn(yi, neg1, ndy);
+            nz[q] = __ffma2_rn(zi, neg1, ndz);
+            // rounding error of s (Fast2Sum) plus the remainder of D
+            const float2 lx = __fadd2_rn(__fadd2_rn(xi, __fadd2_rn(nx[q], dhx)), dlx);
+            const float2 ly = __fadd2_rn(__fadd2_rn(yi, __fadd2_rn(ny[q], dhy)), dly);
+            const float2 lz = __fadd2_rn(__fadd2_rn(zi, __fadd2_rn(nz[q], dhz)), dlz);
+            float2 R2 = __fmul2_rn(nx[q], nx[q]);
+            R2 = __ffma2_rn(ny[q], ny[q], R2);
+            R2 = __ffma2_rn(nz[q], nz[q], R2);
+            ss[q] = R2;
+            const float2 Ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
+            const float2 Ri2 = __fmul2_rn(Ri, Ri);
+            const float2 k1 = __fmul2_rn(__fmul2_rn(M2, Ri), Ri2);
+            float2 proj = __fmul2_rn(nx[q], lx);
+            proj = __ffma2_rn(ny[q], ly, proj);
+            proj = __ffma2_rn(nz[q], lz, proj);
+            const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
+            const float2 nk1 = __fmul2_rn(k1, neg1);
+            px[q] = __ffma2_rn(k2, nx[q], __fmul2_rn(nk1, lx));
+            py[q] = __ffma2_rn(k2, ny[q], __fmul2_rn(nk1, ly));
+            pz[q] = __ffma2_rn(k2, nz[q], __fmul2_rn(nk1, lz));
+        }
+    }
+#pragma unroll 1
+    for (int j0 = 0; j0 < T; j0 += kFoldFar) {
+        float2 p0[NPAIR];  // sum of w^3
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) p0[q] = make_float2(0.f, 0.f);
+#pragma unroll 4
+        for (int j = j0; j < j0 + kFoldFar; ++j) {
+            const float4 A = W.sf[4 * j], B = W.sf[4 * j + 1], C = W.sf[4 * j + 2], E = W.sf[4 * j + 3];
+            const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+            const float2 zj = make_float2(B.x, B.y), kj = make_float2(B.z, B.w);
+            const float2 axj = make_float2(C.x, C.y), ayj = make_float2(C.z, C.w);
+            const float2 azj = make_float2(E.x, E.y), bj = make_float2(E.z, E.w);
+            float4 K = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (CUT) K = W.sk[j];
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                float2 t = __ffma2_rn(kj, ss[q], bj);
+                t = __ffma2_rn(axj, nx[q], t);
+                t = __ffma2_rn(ayj, ny[q], t);
+                t = __ffma2_rn(azj, nz[q], t);
+                const float2 w = make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y));
+                float2 sc = __fmul2_rn(__fmul2_rn(w, w), w);
+                if (CUT) {
+                    const float2 dt = __fadd2_rn(t, make_float2(K.x, K.y));  // k_j (r^2 - (2.6 L)^2)
+                    if (fabsf(dt.x) < K.z || fabsf(dt.y) < K.z) {
+                        sc = cut_decide(sc, dt, K.z, dc, 2 * q, j);
+                    } else {
+                        sc.x = dt.x < 0.f ? sc.x : 0.f;
+                        sc.y = dt.y < 0.f ? sc.y : 0.f;
+                    }
+                }
+                px[q] = __ffma2_rn(sc, xj, px[q]);
+                py[q] = __ffma2_rn(sc, yj, py[q]);
+                pz[q] = __ffma2_rn(sc, zj, pz[q]);
+                p0[q] = __fadd2_rn(p0[q], sc);
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) {
+            // sum of w^3 (o_j - s) = px + n p0
+            const float2 qx = __ffma2_rn(nx[q], p0[q], px[q]);
+            const float2 qy = __ffma2_rn(ny[q], p0[q], py[q]);
+            const float2 qz = __ffma2_rn(nz[q], p0[q], pz[q]);
+            if (act) {
+                kahan2(hx[q], cx[q], qx);
+                kahan2(hy[q], cy[q], qy);
+                kahan2(hz[q], cz[q], qz);
+            }
+            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+        }
+    }
+}
+
+// The terms of one near image for this lane's KF targets with exact
+// separations: for target t, x_j + nL - x_i = (o_j + s'_t) + (r_j + r'_t) with
+// -s'_t = fl(o_i + D) and -r'_t = r_i + remainder(D) + err(fl(o_i + D)), so the
+// separation carries ~1 ulp of its own size; Eq. 4's spline inside h_i + h_j;
+// self pairs and the self's images add nothing.  Sources are read from the
+// global staging (near images are few).  DECIDE: some pairs may fall outside
+// the cut sphere (or the half-box region), so every term is tested, and
+// re-decided in FP64 within the thin bands.
+template <int T, int KF, bool DECIDE>
+__device__ __forceinline__ void exact_image(const float4 *__restrict__ S, const float4 *__restrict__ R,
+                                            const float4 *__restrict__ rdup, const float (&D)[6],
+                                            const WarpSmem<T, KF> &W, const int ti0, const bool self_tile,
+                                            const bool act, const DecideCtx &dc, const float cut2, const float halfL,
+                                            const float L, float2 (&hx)[KF / 2], float2 (&hy)[KF / 2],
+                                            float2 (&hz)[KF / 2], float2 (&cx)[KF / 2], float2 (&cy)[KF / 2],
+                                            float2 (&cz)[KF / 2]) {
+    float nxs[KF], nys[KF], nzs[KF], nrx[KF], nry[KF], nrz[KF], hI[KF];
+#pragma unroll
+    for (int t = 0; t < KF; ++t) {
+        const int64_t gi = dc.gi0 + t;
+        const float4 r0 = rdup[2 * gi], r1 = rdup[2 * gi + 1];
+        const float ox = W.tx[ti0 + t], oy = W.ty[ti0 + t], oz = W.tz[ti0 + t];
+        float e;
+        nxs[t] = -two_sum(ox, D[0], e);
+        nrx[t] = -((r0.x + D[3]) + e);
+        nys[t] = -two_sum(oy, D[1], e);
+        nry[t] = -((r0.z + D[4]) + e);
+        nzs[t] = -two_sum(oz, D[2], e);
+        nrz[t] = -((r1.x + D[5]) + e);
+        hI[t] = r1.z;
+    }
+#pragma unroll 1
+    for (int f0 = 0; f0 < T; f0 += kFoldExact) {
+        float px[KF], py[KF], pz[KF];
+#pragma unroll
+        for (int t = 0; t < KF; ++t) px[t] = py[t] = pz[t] = 0.f;
 #pragma unroll 2
-        for (int j = f0; j < f0 + kFold; ++j) {
+        for (int j = f0; j < f0 + kFoldExact; ++j) {
             const float4 A = S[2 * j], B = S[2 * j + 1];
-            const float4 RA = S[2 * T + 2 * j], RB = S[2 * T + 2 * j + 1];
+            const float4 RA = R[2 * j], RB = R[2 * j + 1];
             if (B.z == 0.f) continue;  // padding source (zero mass)
 #pragma unroll
-            for (int t = 0; t < KI; ++t) {
+            for (int t = 0; t < KF; ++t) {
                 // d = x_j + nL - x_i
                 const float dx = (A.x + nxs[t]) + (RA.x + nrx[t]);
                 const float dy = (A.z + nys[t]) + (RA.z + nry[t]);
                 const float dz = (B.x + nzs[t]) + (RB.x + nrz[t]);
                 const float r2 = dx * dx + dy * dy + dz * dz;
-                bool in = r2 > 0.f && !(self_tile && j == lane * KI + t);  // no self pair, no self images
+                bool in = r2 > 0.f && !(self_tile && j == ti0 + t);  // no self pair, no self images
                 if (DECIDE && in) {
                     bool ambiguous;
-                    if (a.images == 1) {
+                    if (dc.images == 1) {
                         // x_i - x_j - nL = -d in [-L/2, L/2)  <=>  d in (-L/2, L/2]
                         in = dx > -halfL && dx <= halfL && dy > -halfL && dy <= halfL && dz > -halfL && dz <= halfL;
                         const float band = kFaceBand * L;
@@ -150,156 +312,213 @@ __device__ __forceinline__ void image_terms(const float4 *__restrict__ S, const 
                         ambiguous = fabsf(r2 - cut2) < kCutBand * cut2;
                     }
                     if (ambiguous) {
-                        const int64_t gj = J * T + j;
-                        in = gi[t] < a.n && include_f64(a.x[gi[t]], a.y[gi[t]], a.z[gi[t]], a.x[gj], a.y[gj],
-                                                         a.z[gj], nx, ny, nz, a.L, a.images);
+                        const int64_t gi = dc.gi0 + t, gj = dc.gj0 + j;
+                        in = gi < dc.n && gj < dc.n &&
+                             include_f64(dc.x[gi], dc.y[gi], dc.z[gi], dc.x[gj], dc.y[gj], dc.z[gj], dc.nx, dc.ny,
+                                         dc.nz, dc.L, dc.images);
                     }
                 }
                 if (!in) continue;
                 const float H = hI[t] + RB.z;
-                const float ri = rsqrt_f(r2);
-                const float g = (r2 >= H * H) ? ri * ri * ri : spline_over_r_f(r2 * ri, H);
+                const float ri = rsqrt_approx(r2);
+                const float g = (r2 >= H * H) ? ri * ri * ri : spline_over_r_f32(r2 * ri, H);
                 const float sc = B.z * g;
                 px[t] = fmaf(sc, dx, px[t]);
                 py[t] = fmaf(sc, dy, py[t]);
                 pz[t] = fmaf(sc, dz, pz[t]);
             }
         }
+        if (act) {
 #pragma unroll
-        for (int t = 0; t < KI; ++t) {
-            const float p[3] = {px[t], py[t], pz[t]};
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {  // Kahan fold
-                const float y = p[c] - kc[t][c], tt = kh[t][c] + y;
-                kc[t][c] = (tt - kh[t][c]) - y;
-                kh[t][c] = tt;
+            for (int q = 0; q < KF / 2; ++q) {
+                kahan2(hx[q], cx[q], make_float2(px[2 * q], px[2 * q + 1]));
+                kahan2(hy[q], cy[q], make_float2(py[2 * q], py[2 * q + 1]));
+                kahan2(hz[q], cz[q], make_float2(pz[2 * q], pz[2 * q + 1]));
             }
         }
     }
 }
 
-template <int KI>
-__global__ void __launch_bounds__(32 * kWarps) periodic_f32_kernel(const PeriodicArgs a) {
-    constexpr int T = 32 * KI;
-    __shared__ float4 sbuf[kWarps][4 * T];  // per warp: jdup tile [2T] | rdup tile [2T]
+// The shift of image k for this tile pair: FP32 values and remainders.
+__device__ __forceinline__ void image_shift(const float *dh, const float *dl, int nx, int ny, int nz,
+                                            float (&D)[6]) {
+    D[0] = dh[nx + 3];
+    D[1] = dh[10 + ny];
+    D[2] = dh[17 + nz];
+    D[3] = dl[nx + 3];
+    D[4] = dl[10 + ny];
+    D[5] = dl[17 + nz];
+}
+
+// One work item per warp: target tile I (T targets, KF per lane in slots of
+// T / KF lanes) against source tiles [J0, J1) of its chunk, every image.
+template <int T, int KF>
+__global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const PeriodicArgs a) {
+    constexpr int LPI = T / KF;    // lanes per image slot
+    constexpr int IPW = 32 / LPI;  // images per warp step
+    constexpr int NPAIR = KF / 2;
+    static_assert(LPI * IPW == 32 && KF % 2 == 0, "lanes must split into whole image slots");
+    extern __shared__ float4 periodic_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    WarpSmem<T, KF> &W = reinterpret_cast<WarpSmem<T, KF> *>(periodic_smem)[warp];
     const int64_t item = (int64_t)blockIdx.x * kWarps + warp;
-    if (item >= a.ntile * a.nchunk) return;
+    if (item >= a.ntile * a.nchunk) return;  // whole warp; warps of a CTA never synchronise
     const int64_t I = item / a.nchunk, ch = item % a.nchunk;
     const int64_t J0 = ch * a.ntile / a.nchunk, J1 = (ch + 1) * a.ntile / a.nchunk;
-    float4 *S = sbuf[warp];
+    const int g = lane / LPI;           // image slot
+    const int ti0 = (lane % LPI) * KF;  // this lane's first target within the tile
     const float L = (float)a.L;
-    const float cut2 = (float)(2.6 * a.L) * (float)(2.6 * a.L);
+    const double cutd = 2.6 * a.L;
+    const float cut2 = (float)(cutd * cutd);
     const float halfL = 0.5f * L;
     const int nimg = a.images == 1 ? 27 : 343;
+    const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
+    const float mg = 1e-5f * L;  // margin of the FP32 box tests (their rounding is ~1e-7 L)
 
-    // this lane's targets: offsets, residuals, softening, global index
-    float xi[KI], yi[KI], zi[KI], rxi[KI], ryi[KI], rzi[KI], hI[KI];
-    int64_t gi[KI];
-    double acc[KI][3];
-#pragma unroll
-    for (int t = 0; t < KI; ++t) {
-        gi[t] = I * T + lane * KI + t;
-        const float4 p = a.jdup[2 * gi[t]], pz = a.jdup[2 * gi[t] + 1];
-        const float4 r = a.rdup[2 * gi[t]], rz = a.rdup[2 * gi[t] + 1];
-        xi[t] = p.x;
-        yi[t] = p.z;
-        zi[t] = pz.x;
-        rxi[t] = r.x;
-        ryi[t] = r.z;
-        rzi[t] = rz.x;
-        hI[t] = rz.z;
-        acc[t][0] = acc[t][1] = acc[t][2] = 0.0;
+    const int64_t gi0 = I * T + ti0;
+    for (int k = lane; k < T; k += 32) {
+        const float4 p = a.jdup[2 * (I * T + k)], pz = a.jdup[2 * (I * T + k) + 1];
+        W.tx[k] = p.x;
+        W.ty[k] = p.z;
+        W.tz[k] = pz.x;
     }
+#pragma unroll
+    for (int t = 0; t < 3 * KF; ++t) W.acc[t][lane] = 0.0;
     const float4 ci = a.tbox_c[I], ei = a.tbox_e[I];
+    const float eIn = sqrtf(ei.x * ei.x + ei.y * ei.y + ei.z * ei.z);
 
     for (int64_t J = J0; J < J1; ++J) {
         __syncwarp();
-        for (int k = lane; k < 2 * T; k += 32) {
-            S[k] = a.jdup[2 * J * T + k];
-            S[2 * T + k] = a.rdup[2 * J * T + k];
+        const float4 *src = a.fdup + 4 * J * T;
+        for (int k = lane; k < 4 * T; k += 32) W.sf[k] = src[k];
+        const float4 cj = a.tbox_c[J], ej = a.tbox_e[J];
+        if (lane < 21) {
+            // c_I - (c_J + nL) in FP64 per axis and n in [-3, 3], split into FP32 value + remainder
+            const int ax = lane / 7, nn = lane % 7 - 3;
+            const float c0 = ax == 0 ? ci.x : (ax == 1 ? ci.y : ci.z);
+            const float c1 = ax == 0 ? cj.x : (ax == 1 ? cj.y : cj.z);
+            const double d = (double)c0 - ((double)c1 + nn * a.L);
+            const float hi = (float)d;
+            W.dh[lane] = hi;
+            W.dl[lane] = (float)(d - (double)hi);
         }
         __syncwarp();
-        const float4 cj = a.tbox_c[J], ej = a.tbox_e[J];
-        // compensated FP32 sums over all images and sources of tile J, one FP64 add per tile
-        float kh[KI][3], kc[KI][3];
-#pragma unroll
-        for (int t = 0; t < KI; ++t)
-            for (int c = 0; c < 3; ++c) kh[t][c] = kc[t][c] = 0.f;
+        for (int j = lane; j < T; j += 32) {
+            const float kc = W.sf[4 * j + 1].z * cut2;
+            W.sk[j] = make_float4(-kc, -kc, kCutBand * kc, kCutBand * kc);
+        }
+        // sort the candidate images of this tile pair into the three lists
+        const float wx = __fadd_rn(ei.x, ej.x) * up + mg, wy = __fadd_rn(ei.y, ej.y) * up + mg,
+                    wz = __fadd_rn(ei.z, ej.z) * up + mg;
+        const float hs = __fadd_rn(ci.w, cj.w) * up;
+        const float ext = (eIn + sqrtf(ej.x * ej.x + ej.y * ej.y + ej.z * ej.z)) * up;
+        const bool self_tile = (I == J);
+        int nF = 0, nC = 0, nE = 0;
         for (int k0 = 0; k0 < nimg; k0 += 32) {
-            // which images of tile J can hold a term for tile I (box test, FP64), and
-            // which hold every pair of the two tiles (no per-pair decision needed)
-            bool cand = false, all_in = false;
             const int k = k0 + lane;
+            int cls = 0;  // 0 none, 1 far inside, 2 far straddling the cut, 3 near
+            bool allin = false;
             if (k < nimg) {
                 int nx, ny, nz;
                 image_of(k, a.images, nx, ny, nz);
-                const double sx = (double)ci.x - ((double)cj.x + nx * a.L);
-                const double sy = (double)ci.y - ((double)cj.y + ny * a.L);
-                const double sz = (double)ci.z - ((double)cj.z + nz * a.L);
-                const double wx = (double)ei.x + ej.x, wy = (double)ei.y + ej.y, wz = (double)ei.z + ej.z;
-                const double margin = 1e-6 * a.L;
+                const float sx = W.dh[nx + 3], sy = W.dh[10 + ny], sz = W.dh[17 + nz];
+                const float ax_ = fabsf(sx), ay_ = fabsf(sy), az_ = fabsf(sz);
+                const float gx = fmaxf(0.f, ax_ - wx), gy = fmaxf(0.f, ay_ - wy), gz = fmaxf(0.f, az_ - wz);
+                const float fx = ax_ + wx, fy = ay_ + wy, fz = az_ + wz;
+                const float gap2 = gx * gx + gy * gy + gz * gz;
+                bool cand;
                 if (a.images == 1) {
-                    // some pair separation x_i - x_j - nL may lie in [-L/2, L/2]^3
-                    cand = fabs(sx) <= 0.5 * a.L + wx + margin && fabs(sy) <= 0.5 * a.L + wy + margin &&
-                           fabs(sz) <= 0.5 * a.L + wz + margin;
-                    all_in = fabs(sx) + wx < 0.5 * a.L - margin && fabs(sy) + wy < 0.5 * a.L - margin &&
-                             fabs(sz) + wz < 0.5 * a.L - margin;
+                    cand = ax_ <= halfL + wx && ay_ <= halfL + wy && az_ <= halfL + wz;
+                    allin = fx < halfL && fy < halfL && fz < halfL;
                 } else {
-                    const double gx = fmax(0.0, fabs(sx) - wx), gy = fmax(0.0, fabs(sy) - wy),
-                                 gz = fmax(0.0, fabs(sz) - wz);
-                    const double cutm = 2.6 * a.L + margin, cutn = 2.6 * a.L - margin;
-                    cand = gx * gx + gy * gy + gz * gz < cutm * cutm;
-                    const double fx = fabs(sx) + wx, fy = fabs(sy) + wy, fz = fabs(sz) + wz;
-                    all_in = fx * fx + fy * fy + fz * fz < cutn * cutn;
+                    cand = gap2 < cut2 * up;
+                    allin = fx * fx + fy * fy + fz * fz < cut2 * dn;
+                }
+                if (cand) {
+                    const float dist2 = sx * sx + sy * sy + sz * sz;
+                    const float scale = sqrtf(dist2) + ext;
+                    const bool near =
+                        self_tile || gap2 <= hs * hs || ext * ext > dist2 * dn || gap2 < kAlpha2 * scale * scale;
+                    cls = near ? 3 : (allin ? 1 : (a.images == 1 ? 3 : 2));
                 }
             }
-            unsigned mask = __ballot_sync(0xffffffffu, cand);
-            const unsigned inside = __ballot_sync(0xffffffffu, all_in);
-            while (mask) {
-                const int b = __ffs(mask) - 1;
-                mask &= mask - 1;
-                int nx, ny, nz;
-                image_of(k0 + b, a.images, nx, ny, nz);
-                // c_I - (c_J + nL) in FP64, split into an FP32 value and its remainder
-                const double dcx = (double)ci.x - ((double)cj.x + nx * a.L);
-                const double dcy = (double)ci.y - ((double)cj.y + ny * a.L);
-                const double dcz = (double)ci.z - ((double)cj.z + nz * a.L);
-                const float hx = (float)dcx, hy = (float)dcy, hz = (float)dcz;
-                const float lx = (float)(dcx - hx), ly = (float)(dcy - hy), lz = (float)(dcz - hz);
-                const bool self_tile = (J == I) && (nx | ny | nz);
-                const bool decide = !((inside >> b) & 1u);
-                // -(s), s = fl(o_i + dc), and -(r_i + remainder(dc) + err(s)), per target
-                float nxs[KI], nys[KI], nzs[KI], nrx[KI], nry[KI], nrz[KI];
+            const unsigned lt = (1u << lane) - 1u;
+            const unsigned bF = __ballot_sync(0xffffffffu, cls == 1);
+            const unsigned bC = __ballot_sync(0xffffffffu, cls == 2);
+            const unsigned bE = __ballot_sync(0xffffffffu, cls == 3);
+            if (cls == 1)
+                W.lf[nF + __popc(bF & lt)] = (uint16_t)k;
+            else if (cls == 2)
+                W.lc[nC + __popc(bC & lt)] = (uint16_t)k;
+            else if (cls == 3)
+                W.le[nE + __popc(bE & lt)] = (uint16_t)(k | (allin ? kAllIn : 0));
+            nF += __popc(bF);
+            nC += __popc(bC);
+            nE += __popc(bE);
+        }
+        __syncwarp();
+
+        // compensated FP32 sums over every image of tile J, one FP64 add per tile
+        float2 hx[NPAIR], hy[NPAIR], hz[NPAIR], cx[NPAIR], cy[NPAIR], cz[NPAIR];
 #pragma unroll
-                for (int t = 0; t < KI; ++t) {
-                    float e;
-                    nxs[t] = -two_sum_f(xi[t], hx, e);
-                    nrx[t] = -((rxi[t] + lx) + e);
-                    nys[t] = -two_sum_f(yi[t], hy, e);
-                    nry[t] = -((ryi[t] + ly) + e);
-                    nzs[t] = -two_sum_f(zi[t], hz, e);
-                    nrz[t] = -((rzi[t] + lz) + e);
-                }
-                if (decide)
-                    image_terms<KI, T, true>(S, a, nxs, nys, nzs, nrx, nry, nrz, hI, gi, J, nx, ny, nz, self_tile,
-                                             lane, cut2, halfL, L, kh, kc);
-                else
-                    image_terms<KI, T, false>(S, a, nxs, nys, nzs, nrx, nry, nrz, hI, gi, J, nx, ny, nz, self_tile,
-                                              lane, cut2, halfL, L, kh, kc);
-            }
+        for (int q = 0; q < NPAIR; ++q)
+            hx[q] = hy[q] = hz[q] = cx[q] = cy[q] = cz[q] = make_float2(0.f, 0.f);
+        DecideCtx dc{a.x, a.y, a.z, a.n, a.L, a.images, 0, 0, 0, gi0, J * T};
+        for (int b = 0; b < nF; b += IPW) {
+            const bool act = b + g < nF;  // idle slots repeat the step's first image and add nothing
+            const int k = W.lf[act ? b + g : b];
+            float D[6];
+            image_of(k, a.images, dc.nx, dc.ny, dc.nz);
+            image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
+            far_image<T, NPAIR, false>(W, D, ej.w, ti0, act, dc, hx, hy, hz, cx, cy, cz);
+        }
+        for (int b = 0; b < nC; b += IPW) {
+            const bool act = b + g < nC;
+            const int k = W.lc[act ? b + g : b];
+            float D[6];
+            image_of(k, a.images, dc.nx, dc.ny, dc.nz);
+            image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
+            far_image<T, NPAIR, true>(W, D, ej.w, ti0, act, dc, hx, hy, hz, cx, cy, cz);
+        }
+        const float4 *S = a.jdup + 2 * J * T, *R = a.rdup + 2 * J * T;
+        for (int b = 0; b < nE; b += IPW) {
+            const bool act = b + g < nE;
+            const int code = W.le[act ? b + g : b];
+            float D[6];
+            image_of(code & 0x1ff, a.images, dc.nx, dc.ny, dc.nz);
+            image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
+            if (code & kAllIn)
+                exact_image<T, KF, false>(S, R, a.rdup, D, W, ti0, self_tile, act, dc, cut2, halfL, L, hx,
+                                          hy, hz, cx, cy, cz);
+            else
+                exact_image<T, KF, true>(S, R, a.rdup, D, W, ti0, self_tile, act, dc, cut2, halfL, L, hx,
+                                         hy, hz, cx, cy, cz);
         }
 #pragma unroll
-        for (int t = 0; t < KI; ++t)
-            for (int c = 0; c < 3; ++c) acc[t][c] += (double)kh[t][c] - (double)kc[t][c];
+        for (int q = 0; q < NPAIR; ++q) {
+            // value = hi - c, the compensation kept negated
+            W.acc[2 * q][lane] += (double)hx[q].x + (double)cx[q].x;
+            W.acc[2 * q + 1][lane] += (double)hx[q].y + (double)cx[q].y;
+            W.acc[KF + 2 * q][lane] += (double)hy[q].x + (double)cy[q].x;
+            W.acc[KF + 2 * q + 1][lane] += (double)hy[q].y + (double)cy[q].y;
+            W.acc[2 * KF + 2 * q][lane] += (double)hz[q].x + (double)cz[q].x;
+            W.acc[2 * KF + 2 * q + 1][lane] += (double)hz[q].y + (double)cz[q].y;
+        }
     }
-    double *P = a.item_part + (size_t)item * 3 * T;
+    // slots hold the same targets: add them in a fixed order (slot 0 first)
+    __syncwarp();
+    if (g == 0) {
+        double *P = a.item_part + (size_t)item * 3 * T;
 #pragma unroll
-    for (int t = 0; t < KI; ++t) {
-        const int li = lane * KI + t;
-        P[li] = acc[t][0];
-        P[T + li] = acc[t][1];
-        P[2 * T + li] = acc[t][2];
+        for (int t = 0; t < KF; ++t) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double v = W.acc[c * KF + t][lane];
+#pragma unroll
+                for (int s = 1; s < IPW; ++s) v += W.acc[c * KF + t][lane + s * LPI];
+                P[c * T + ti0 + t] = v;
+            }
+        }
     }
 }
 
@@ -395,16 +614,54 @@ __global__ void __launch_bounds__(128) periodic_f64_kernel(int64_t n, const doub
     }
 }
 
+template <int T, int KF>
+cudaError_t launch_tile(const PeriodicArgs &a, unsigned blocks, cudaStream_t st) {
+    const size_t smem = sizeof(WarpSmem<T, KF>) * kWarps;
+    // the shared-memory opt-in is set outside graph capture (the first force
+    // evaluation of a context always runs outside one)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaError_t e = cudaStreamIsCapturing(st, &cs);
+    if (e != cudaSuccess) return e;
+    if (cs == cudaStreamCaptureStatusNone) {
+        e = cudaFuncSetAttribute(periodic_f32_kernel<T, KF>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    periodic_f32_kernel<T, KF><<<blocks, 32 * kWarps, smem, st>>>(a);
+    return cudaGetLastError();
+}
+
 }  // namespace
 
-int64_t periodic_chunks(int64_t ntile) { return ntile < 8 ? ntile : 8; }
+// Enough work items (one warp each) for several waves of 16 warps per SM, at
+// most 64 chunks of source tiles per target tile.
+int64_t periodic_chunks(int64_t ntile, int num_sms) {
+    const int64_t want = (int64_t)std::max(num_sms, 1) * 16 * 8;
+    int64_t c = (want + ntile - 1) / ntile;
+    c = std::min<int64_t>(c, 64);
+    c = std::min<int64_t>(c, ntile);
+    return std::max<int64_t>(c, 1);
+}
+
+// Upper bound over every tile count x <= np / T: x * periodic_chunks(x) is at
+// most min(64 x, want + x).
+size_t periodic_part_elems(int64_t np, int num_sms) {
+    const int64_t want = (int64_t)std::max(num_sms, 1) * 16 * 8;
+    size_t m = 0;
+    for (int T : {64, 128, 192}) {
+        const int64_t nt = (np + T - 1) / T;
+        m = std::max(m, (size_t)std::min<int64_t>(64 * nt, want + nt) * 3 * T);
+    }
+    return m;
+}
 
 cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                int images, double G, double *item_part, double *ax, double *ay, double *az,
-                                cudaStream_t st) {
+                                int images, double G, double *item_part, int num_sms, double *ax, double *ay,
+                                double *az, cudaStream_t st) {
+    if (!s.fdup) return cudaErrorInvalidValue;
     PeriodicArgs a;
     a.jdup = s.jdup;
     a.rdup = s.rdup;
+    a.fdup = s.fdup;
     a.tbox_c = s.tbox_c;
     a.tbox_e = s.tbox_e;
     a.x = x;
@@ -412,19 +669,19 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
     a.z = z;
     a.item_part = item_part;
     a.ntile = s.ntile;
-    a.nchunk = periodic_chunks(s.ntile);
+    a.nchunk = periodic_chunks(s.ntile, num_sms);
     a.n = s.n;
     a.L = L;
     a.images = images;
     const int64_t items = a.ntile * a.nchunk;
     const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
+    cudaError_t e;
     switch (s.T) {
-        case 64: periodic_f32_kernel<2><<<blocks, 32 * kWarps, 0, st>>>(a); break;
-        case 128: periodic_f32_kernel<4><<<blocks, 32 * kWarps, 0, st>>>(a); break;
-        case 192: periodic_f32_kernel<6><<<blocks, 32 * kWarps, 0, st>>>(a); break;
+        case 64: e = launch_tile<64, 4>(a, blocks, st); break;
+        case 128: e = launch_tile<128, 4>(a, blocks, st); break;
+        case 192: e = launch_tile<192, 6>(a, blocks, st); break;
         default: return cudaErrorInvalidValue;
     }
-    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     periodic_reduce_kernel<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(item_part, s.n, s.T, a.nchunk, G, ax, ay,
                                                                          az);

@@ -129,22 +129,25 @@ cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *par
                          const NearScratch &nr, double G, double *ax, double *ay, double *az,
                          cudaStream_t st);
 
-// Periodic pair term (Eq. 2 with Eq. 5).  FP32 path on the tile staging:
-// work items (target tile, chunk of source tiles) write FP64 partials
-// item_part [ntile * nchunk][3][T] (nchunk = periodic_chunks(ntile) <= 8),
-// then a reduction applies G into ax, ay, az (sorted order).
+// Periodic pair term (Eq. 2 with Eq. 5).  FP32 path on the tile staging
+// (including the far-field expansion layout fdup): work items (target tile,
+// chunk of source tiles) write FP64 partials item_part [ntile * nchunk][3][T]
+// (nchunk = periodic_chunks(ntile, num_sms)), then a reduction applies G into
+// ax, ay, az (sorted order).
 struct PeriodicArgs {
-    const float4 *jdup, *rdup, *tbox_c, *tbox_e;
+    const float4 *jdup, *rdup, *fdup, *tbox_c, *tbox_e;
     const double *x, *y, *z;  // FP64 sorted positions: decisions near the cut / half-box faces
     double *item_part;
     int64_t ntile, nchunk, n;
     double L;
     int images;
 };
-int64_t periodic_chunks(int64_t ntile);
+int64_t periodic_chunks(int64_t ntile, int num_sms);
+// Largest item_part size (doubles) any tile size needs for np padded particles.
+size_t periodic_part_elems(int64_t np, int num_sms);
 cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                int images, double G, double *item_part, double *ax, double *ay, double *az,
-                                cudaStream_t st);
+                                int images, double G, double *item_part, int num_sms, double *ax, double *ay,
+                                double *az, cudaStream_t st);
 cudaError_t launch_periodic_f64(int64_t n, const double *x, const double *y, const double *z, const double *m,
                                 const double *h, double G, double L, int images, double *ax, double *ay,
                                 double *az, cudaStream_t st);

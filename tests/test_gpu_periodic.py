@@ -41,9 +41,10 @@ def clumpy_box(seed, n, L):
     return pos, m, h
 
 
-def periodic_sim(pos, m, h, L, images, prec, vel=None, a0=1.0, resort_every=8):
+def periodic_sim(pos, m, h, L, images, prec, vel=None, a0=1.0, resort_every=8, variant=None):
+    tile = 0 if variant is None else steps.steps_variants().index(variant) + 1
     cfg = steps.make_config(mode=steps.STEPS_PERIODIC, prec=prec, G=1.0, Om=1.0, OL=0.0, box=L, images=images,
-                            resort_every=resort_every)
+                            resort_every=resort_every, tile_override=tile)
     return steps.Simulation(pos, np.zeros_like(pos) if vel is None else vel, m, soft=h, a0=a0, cfg=cfg)
 
 
@@ -66,6 +67,47 @@ def test_periodic_forces_match_oracle(images, n):
     sim.close()
     rms = math.sqrt(np.mean(e ** 2))
     print("n=%d images=%d FP32 rms %.2e max %.2e" % (n, images, rms, e.max()))
+    assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
+
+
+@pytest.mark.parametrize("variant", ["comp_ki4_w4_u4", "exp_ki6_w4_u4"])
+@pytest.mark.parametrize("images", [0, 1])
+def test_periodic_tile_sizes(variant, images):
+    """128- and 192-particle tiles (one image per warp step, 4 or 6 targets per
+    lane) against the oracle; the default at these sizes is 64-particle tiles
+    with two image slots per warp."""
+    L, n = 2.0, 3000
+    pos, m, h = clumpy_box(40 + images, n, L)
+    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images)
+    sim = periodic_sim(pos, m, h, L, images, steps.STEPS_F32_COMP, variant=variant)
+    e = rel_err(sim.forces(), ref)
+    sim.close()
+    rms = math.sqrt(np.mean(e ** 2))
+    print("%s images=%d FP32 rms %.2e max %.2e" % (variant, images, rms, e.max()))
+    assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
+
+
+@pytest.mark.parametrize("kind", ["uniform", "clumpy"])
+def test_periodic_16k_sampled_targets(kind):
+    """The size the periodic throughput is measured at (N = 16,384, L = 1, cut
+    image sum): FP32 against the oracle on 64 sampled targets.  Here the far
+    images dominate (~53 of the ~74 images per pair lie wholly inside the cut
+    sphere) and the sum cancels heavily in the uniform box."""
+    L, n = 1.0, 16384
+    rng = np.random.default_rng(16)
+    if kind == "uniform":
+        pos = rng.random((n, 3)) * L
+        m = np.full(n, 1.0 / n)
+        h = np.full(n, 0.02 * L / n ** (1.0 / 3.0))
+    else:
+        pos, m, h = clumpy_box(16, n, L)
+    tg = np.sort(rng.choice(n, 64, replace=False))
+    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, 0, targets=tg)
+    sim = periodic_sim(pos, m, h, L, 0, steps.STEPS_F32_COMP)
+    e = rel_err(sim.forces()[tg], ref)
+    sim.close()
+    rms = math.sqrt(np.mean(e ** 2))
+    print("N=16384 %s FP32 rms %.2e max %.2e" % (kind, rms, e.max()))
     assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
 
 
