@@ -13,10 +13,11 @@
 //  * far, wholly inside the cut sphere (or the half-box region): every pair is
 //    a Newtonian term; summed by expansion about the source tile's centre
 //    with packed FP32x2 arithmetic (10 lane operations + 1 MUFU per term), the
-//    target shift's rounding undone with the tile's monopole tidal tensor;
+//    target shift's rounding undone to first order from the kept terms;
 //  * far, straddling the cut sphere: the same, and each term is kept when
-//    k_j r^2 < k_j (2.6 L)^2; terms within a thin band of the cut are decided
-//    again in FP64 from the FP64 positions with the definition's expression;
+//    k_j r^2 < k_j (2.6 L)^2 (branch-free); terms within a thin band of the
+//    cut are decided again in FP64 from the FP64 positions with the
+//    definition's expression;
 //  * near (some pair may lie inside h_i + h_j, or the tile pair is too close
 //    for the expansion, or I = J): exact separations to ~1 ulp of their own
 //    size, the full spline of Eq. 4, and per-pair FP64 re-decisions in the
@@ -117,57 +118,31 @@ struct DecideCtx {
     int64_t gj0;     // global index of the source tile's first particle
 };
 
-// Terms of a straddling far image within the FP32 band of the cut: the
-// definition's FP64 decision for each of the two packed targets (2 q, 2 q + 1).
-__device__ __noinline__ float2 cut_decide(float2 sc, const float2 dt, const float band, const DecideCtx dc,
-                                          const int t0, const int j) {
-    const int64_t gj = dc.gj0 + j;
-#pragma unroll
-    for (int e = 0; e < 2; ++e) {
-        const float d = e ? dt.y : dt.x;
-        const int64_t gi = dc.gi0 + t0 + e;
-        bool in;
-        if (fabsf(d) < band)
-            in = gi < dc.n && gj < dc.n &&
-                 include_f64(dc.x[gi], dc.y[gi], dc.z[gi], dc.x[gj], dc.y[gj], dc.z[gj], dc.nx, dc.ny, dc.nz, dc.L,
-                             0);
-        else
-            in = d < 0.f;
-        if (!in) {
-            if (e)
-                sc.y = 0.f;
-            else
-                sc.x = 0.f;
-        }
-    }
-    return sc;
-}
-
 // The terms of one far image (source tile J shifted by nL) for this lane's KF
 // targets, every pair Newtonian.  With s = fl(o_i + D) the target relative to
 // the shifted source tile's centre, n = -s and k_j = m_j^(-2/3) rounded to FP32,
 //     k_j |o_j - s|^2 = k_j |n|^2 + k_j |o_j|^2 + (2 k_j o_j) . n
 // (a four-step FMA chain on the staged coefficients), and
-// (k_j |o_j - s|^2)^(-3/2) = m_j / |x_j + nL - x_i|^3.  The rounding of the
-// target shift, l = (o_i + D) - s, is the same for every source of the tile; it
-// is undone to first order with the tile's monopole tidal tensor,
-// p += M (3 n (n.l) / R^5 - l / R^3).  CUT: the image straddles the cut
-// sphere; a term counts when k_j r^2 < k_j (2.6 L)^2, and terms within a
-// relative band of 4e-6 of the cut are decided in FP64 (cut_decide).
+// w^3 = (k_j |o_j - s|^2)^(-3/2) = m_j / |x_j + nL - x_i|^3; the image adds
+// sum_j w^3 (o_j - s) = sum_j w^3 o_j + n sum_j w^3.
+// The rounding of the target shift, l = (o_i + D) - s, is the same for every
+// source of the tile; to first order it changes each term by
+// w^3 (3 n (n.l) / R^2 - l) (R = |s|, the tile small against R), so the image
+// adds (3 n (n.l) / R^2 - l) sum_j w^3 over the terms it keeps.
+// CUT: the image straddles the cut sphere; a term counts when
+// k_j r^2 < k_j (2.6 L)^2.  Terms within a relative band of 4e-6 of the cut
+// are left out of the branch-free loop, flagged, and after the fold decided in
+// FP64 from the FP64 positions with the definition's expression.
 template <int T, int NPAIR, bool CUT>
-__device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const float (&D)[6], const float M,
-                                          const int ti0, const bool act, const DecideCtx &dc,
-                                          float2 (&hx)[NPAIR], float2 (&hy)[NPAIR], float2 (&hz)[NPAIR],
-                                          float2 (&cx)[NPAIR], float2 (&cy)[NPAIR], float2 (&cz)[NPAIR]) {
+__device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const float (&D)[6], const int ti0,
+                                          const bool act, const DecideCtx &dc, float2 (&hx)[NPAIR],
+                                          float2 (&hy)[NPAIR], float2 (&hz)[NPAIR], float2 (&cx)[NPAIR],
+                                          float2 (&cy)[NPAIR], float2 (&cz)[NPAIR]) {
     const float2 neg1 = make_float2(-1.f, -1.f);
-    float2 nx[NPAIR], ny[NPAIR], nz[NPAIR], ss[NPAIR];
-    float2 px[NPAIR], py[NPAIR], pz[NPAIR];  // sum of w^3 o_j (starts at the shift correction)
+    float2 nx[NPAIR], ny[NPAIR], nz[NPAIR], ss[NPAIR], pw[NPAIR];  // pw: sum of w^3 over the image
     {
-        const float2 dhx = make_float2(D[0], D[0]), dhy = make_float2(D[1], D[1]), dhz = make_float2(D[2], D[2]);
-        const float2 dlx = make_float2(D[3], D[3]), dly = make_float2(D[4], D[4]), dlz = make_float2(D[5], D[5]);
         const float2 ndx = make_float2(-D[0], -D[0]), ndy = make_float2(-D[1], -D[1]),
                      ndz = make_float2(-D[2], -D[2]);
-        const float2 M2 = make_float2(M, M);
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             const float2 xi = *reinterpret_cast<const float2 *>(&W.tx[ti0 + 2 * q]);
@@ -176,32 +151,18 @@ __device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const
             nx[q] = __ffma2_rn(xi, neg1, ndx);
             ny[q] = __ffma2_rn(yi, neg1, ndy);
             nz[q] = __ffma2_rn(zi, neg1, ndz);
-            // rounding error of s (Fast2Sum) plus the remainder of D
-            const float2 lx = __fadd2_rn(__fadd2_rn(xi, __fadd2_rn(nx[q], dhx)), dlx);
-            const float2 ly = __fadd2_rn(__fadd2_rn(yi, __fadd2_rn(ny[q], dhy)), dly);
-            const float2 lz = __fadd2_rn(__fadd2_rn(zi, __fadd2_rn(nz[q], dhz)), dlz);
             float2 R2 = __fmul2_rn(nx[q], nx[q]);
             R2 = __ffma2_rn(ny[q], ny[q], R2);
-            R2 = __ffma2_rn(nz[q], nz[q], R2);
-            ss[q] = R2;
-            const float2 Ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
-            const float2 Ri2 = __fmul2_rn(Ri, Ri);
-            const float2 k1 = __fmul2_rn(__fmul2_rn(M2, Ri), Ri2);
-            float2 proj = __fmul2_rn(nx[q], lx);
-            proj = __ffma2_rn(ny[q], ly, proj);
-            proj = __ffma2_rn(nz[q], lz, proj);
-            const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
-            const float2 nk1 = __fmul2_rn(k1, neg1);
-            px[q] = __ffma2_rn(k2, nx[q], __fmul2_rn(nk1, lx));
-            py[q] = __ffma2_rn(k2, ny[q], __fmul2_rn(nk1, ly));
-            pz[q] = __ffma2_rn(k2, nz[q], __fmul2_rn(nk1, lz));
+            ss[q] = __ffma2_rn(nz[q], nz[q], R2);
+            pw[q] = make_float2(0.f, 0.f);
         }
     }
 #pragma unroll 1
     for (int j0 = 0; j0 < T; j0 += kFoldFar) {
-        float2 p0[NPAIR];  // sum of w^3
+        float2 px[NPAIR], py[NPAIR], pz[NPAIR], p0[NPAIR];  // sums of w^3 o_j and of w^3
 #pragma unroll
-        for (int q = 0; q < NPAIR; ++q) p0[q] = make_float2(0.f, 0.f);
+        for (int q = 0; q < NPAIR; ++q) px[q] = py[q] = pz[q] = p0[q] = make_float2(0.f, 0.f);
+        bool amb = false;  // some term of this lane lies in the band around the cut
 #pragma unroll 4
         for (int j = j0; j < j0 + kFoldFar; ++j) {
             const float4 A = W.sf[4 * j], B = W.sf[4 * j + 1], C = W.sf[4 * j + 2], E = W.sf[4 * j + 3];
@@ -217,21 +178,55 @@ __device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const
                 t = __ffma2_rn(axj, nx[q], t);
                 t = __ffma2_rn(ayj, ny[q], t);
                 t = __ffma2_rn(azj, nz[q], t);
-                const float2 w = make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y));
-                float2 sc = __fmul2_rn(__fmul2_rn(w, w), w);
+                float2 w = make_float2(rsqrt_approx(t.x), rsqrt_approx(t.y));
                 if (CUT) {
                     const float2 dt = __fadd2_rn(t, make_float2(K.x, K.y));  // k_j (r^2 - (2.6 L)^2)
-                    if (fabsf(dt.x) < K.z || fabsf(dt.y) < K.z) {
-                        sc = cut_decide(sc, dt, K.z, dc, 2 * q, j);
-                    } else {
-                        sc.x = dt.x < 0.f ? sc.x : 0.f;
-                        sc.y = dt.y < 0.f ? sc.y : 0.f;
-                    }
+                    amb = amb | (fabsf(dt.x) < K.z) | (fabsf(dt.y) < K.z);
+                    w.x = dt.x <= -K.z ? w.x : 0.f;
+                    w.y = dt.y <= -K.z ? w.y : 0.f;
                 }
+                const float2 sc = __fmul2_rn(__fmul2_rn(w, w), w);
                 px[q] = __ffma2_rn(sc, xj, px[q]);
                 py[q] = __ffma2_rn(sc, yj, py[q]);
                 pz[q] = __ffma2_rn(sc, zj, pz[q]);
                 p0[q] = __fadd2_rn(p0[q], sc);
+            }
+        }
+        if (CUT && __any_sync(0xffffffffu, amb) && amb) {
+            // the band terms of this fold, decided in FP64
+            for (int j = j0; j < j0 + kFoldFar; ++j) {
+                const float4 A = W.sf[4 * j], B = W.sf[4 * j + 1], C = W.sf[4 * j + 2], E = W.sf[4 * j + 3];
+                const float4 K = W.sk[j];
+                const int64_t gj = dc.gj0 + j;
+#pragma unroll
+                for (int q = 0; q < NPAIR; ++q) {
+                    float2 t = __ffma2_rn(make_float2(B.z, B.w), ss[q], make_float2(E.z, E.w));
+                    t = __ffma2_rn(make_float2(C.x, C.y), nx[q], t);
+                    t = __ffma2_rn(make_float2(C.z, C.w), ny[q], t);
+                    t = __ffma2_rn(make_float2(E.x, E.y), nz[q], t);
+                    const float2 dt = __fadd2_rn(t, make_float2(K.x, K.y));
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const int64_t gi = dc.gi0 + 2 * q + e;
+                        if (fabsf(e ? dt.y : dt.x) < K.z && gi < dc.n && gj < dc.n &&
+                            include_f64(dc.x[gi], dc.y[gi], dc.z[gi], dc.x[gj], dc.y[gj], dc.z[gj], dc.nx, dc.ny,
+                                        dc.nz, dc.L, 0)) {
+                            const float w = rsqrt_approx(e ? t.y : t.x);
+                            const float sc = w * w * w;
+                            if (e) {
+                                px[q].y = fmaf(sc, A.x, px[q].y);
+                                py[q].y = fmaf(sc, A.z, py[q].y);
+                                pz[q].y = fmaf(sc, B.x, pz[q].y);
+                                p0[q].y += sc;
+                            } else {
+                                px[q].x = fmaf(sc, A.x, px[q].x);
+                                py[q].x = fmaf(sc, A.z, py[q].x);
+                                pz[q].x = fmaf(sc, B.x, pz[q].x);
+                                p0[q].x += sc;
+                            }
+                        }
+                    }
+                }
             }
         }
 #pragma unroll
@@ -245,7 +240,33 @@ __device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const
                 kahan2(hy[q], cy[q], qy);
                 kahan2(hz[q], cz[q], qz);
             }
-            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+            pw[q] = __fadd2_rn(pw[q], p0[q]);
+        }
+    }
+    // first-order correction of the target shift's rounding
+    const float2 dhx = make_float2(D[0], D[0]), dhy = make_float2(D[1], D[1]), dhz = make_float2(D[2], D[2]);
+    const float2 dlx = make_float2(D[3], D[3]), dly = make_float2(D[4], D[4]), dlz = make_float2(D[5], D[5]);
+#pragma unroll
+    for (int q = 0; q < NPAIR; ++q) {
+        const float2 xi = *reinterpret_cast<const float2 *>(&W.tx[ti0 + 2 * q]);
+        const float2 yi = *reinterpret_cast<const float2 *>(&W.ty[ti0 + 2 * q]);
+        const float2 zi = *reinterpret_cast<const float2 *>(&W.tz[ti0 + 2 * q]);
+        // l: rounding error of s (Fast2Sum) plus the remainder of D
+        const float2 lx = __fadd2_rn(__fadd2_rn(xi, __fadd2_rn(nx[q], dhx)), dlx);
+        const float2 ly = __fadd2_rn(__fadd2_rn(yi, __fadd2_rn(ny[q], dhy)), dly);
+        const float2 lz = __fadd2_rn(__fadd2_rn(zi, __fadd2_rn(nz[q], dhz)), dlz);
+        float2 proj = __fmul2_rn(nx[q], lx);
+        proj = __ffma2_rn(ny[q], ly, proj);
+        proj = __ffma2_rn(nz[q], lz, proj);
+        const float2 ri = make_float2(rsqrt_approx(ss[q].x), rsqrt_approx(ss[q].y));
+        const float2 c3 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), proj), __fmul2_rn(ri, ri));
+        const float2 qx = __fmul2_rn(__ffma2_rn(c3, nx[q], __fmul2_rn(lx, neg1)), pw[q]);
+        const float2 qy = __fmul2_rn(__ffma2_rn(c3, ny[q], __fmul2_rn(ly, neg1)), pw[q]);
+        const float2 qz = __fmul2_rn(__ffma2_rn(c3, nz[q], __fmul2_rn(lz, neg1)), pw[q]);
+        if (act) {
+            kahan2(hx[q], cx[q], qx);
+            kahan2(hy[q], cy[q], qy);
+            kahan2(hz[q], cz[q], qz);
         }
     }
 }
@@ -470,7 +491,7 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
             float D[6];
             image_of(k, a.images, dc.nx, dc.ny, dc.nz);
             image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
-            far_image<T, NPAIR, false>(W, D, ej.w, ti0, act, dc, hx, hy, hz, cx, cy, cz);
+            far_image<T, NPAIR, false>(W, D, ti0, act, dc, hx, hy, hz, cx, cy, cz);
         }
         for (int b = 0; b < nC; b += IPW) {
             const bool act = b + g < nC;
@@ -478,7 +499,7 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
             float D[6];
             image_of(k, a.images, dc.nx, dc.ny, dc.nz);
             image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
-            far_image<T, NPAIR, true>(W, D, ej.w, ti0, act, dc, hx, hy, hz, cx, cy, cz);
+            far_image<T, NPAIR, true>(W, D, ti0, act, dc, hx, hy, hz, cx, cy, cz);
         }
         const float4 *S = a.jdup + 2 * J * T, *R = a.rdup + 2 * J * T;
         for (int b = 0; b < nE; b += IPW) {
