@@ -453,8 +453,19 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-ensemble", action="store_true")
     ap.add_argument("--no-periodic", action="store_true")
+    ap.add_argument("--periodic-only", action="store_true",
+                    help="time only the periodic-mode force evaluations (one JSON line; not the bench line)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.periodic_only:
+        import torch
+
+        import paper_1811_05903_gb300.build as libbuild
+        from paper_1811_05903_gb300 import steps
+        torch.cuda.set_device(0)
+        libbuild.build()
+        steps.load()
+        print(json.dumps({"periodic": periodic_throughput(steps)}))
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_ours(args)

@@ -18,10 +18,15 @@
 //    k_j r^2 < k_j (2.6 L)^2 (branch-free); terms within a thin band of the
 //    cut are decided again in FP64 from the FP64 positions with the
 //    definition's expression;
-//  * near (some pair may lie inside h_i + h_j, or the tile pair is too close
-//    for the expansion, or I = J): exact separations to ~1 ulp of their own
-//    size, the full spline of Eq. 4, and per-pair FP64 re-decisions in the
-//    thin bands around the cut sphere or the half-box faces.
+//  * explicit: every pair Newtonian, but the tiles are too close for the
+//    expansion's first-order shift correction, or a quasi-periodic image
+//    straddles the half-box faces: separations to ~1 ulp of their own size
+//    (offset residuals and the exact rounding error of the shifted target),
+//    packed FP32x2, a branch-free boundary test with FP64 re-decisions in the
+//    thin bands;
+//  * near (some pair may lie inside h_i + h_j, or I = J): the same
+//    separations, scalar, with the full spline of Eq. 4 and per-pair FP64
+//    re-decisions in the bands.
 // Each warp owns one target tile and a chunk of source tiles (a work item);
 // lanes are grouped into image slots so that one warp runs 32 / (T / KF)
 // images at once with KF targets per lane and the source loads are shared
@@ -46,6 +51,7 @@ namespace {
 constexpr int kWarps = 4;            // independent work items (warps) per CTA
 constexpr int kFoldFar = 32;         // sources per FP32 partial before a Kahan fold (far images)
 constexpr int kFoldExact = 8;        // the same on the exact (near) path
+constexpr int kFoldExplicit = 16;    // the same on the explicit-separation path
 constexpr float kCutBand = 4e-6f;    // relative band around (2.6 L)^2 decided in FP64
 constexpr float kFaceBand = 2e-6f;   // band around +-L/2 (in units of L) decided in FP64
 constexpr float kAlpha2 = 0.03125f * 0.03125f;  // expansion needs gap >= alpha (distance + extents)
@@ -60,7 +66,7 @@ struct WarpSmem {
     double acc[3 * KF][32];    // FP64 sums of this lane's targets, [component * KF + target][lane]
     float tx[T], ty[T], tz[T]; // tile I: target offsets
     float dh[24], dl[24];      // [axis * 7 + n + 3]: FP32 value and remainder of c_I - (c_J + nL)
-    uint16_t lf[kListCap], lc[kListCap], le[kListCap];  // far-inside, far-straddling, near images
+    uint16_t lf[kListCap], lc[kListCap], le[kListCap], lx[kListCap];  // far inside / straddling, near, explicit
 };
 
 // Image k of the candidate table: cut sum |n_c| <= 3 (7^3 entries; a term needs
@@ -132,7 +138,8 @@ struct DecideCtx {
 // CUT: the image straddles the cut sphere; a term counts when
 // k_j r^2 < k_j (2.6 L)^2.  Terms within a relative band of 4e-6 of the cut
 // are left out of the branch-free loop, flagged, and after the fold decided in
-// FP64 from the FP64 positions with the definition's expression.
+// FP64 from the FP64 positions with the definition's expression (a warp vote:
+// the whole warp calls this with the same CUT).
 template <int T, int NPAIR, bool CUT>
 __device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const float (&D)[6], const int ti0,
                                           const bool act, const DecideCtx &dc, float2 (&hx)[NPAIR],
@@ -360,6 +367,141 @@ __device__ __forceinline__ void exact_image(const float4 *__restrict__ S, const 
     }
 }
 
+// The terms of one image whose pairs are all Newtonian (no pair within
+// h_i + h_j, no self pair) but which the expansion form does not take: tiles
+// too close for its first-order shift correction, or a quasi-periodic image
+// straddling the half-box faces.  Separations as on the exact path,
+// x_j + nL - x_i = (o_j + s'_t) + (r_j + r'_t), packed two targets at a time
+// (FP32x2).  DECIDE: a term counts when r^2 < (2.6 L)^2 (cut sum) or when
+// max_c |d_c| < L/2 (QUASI); terms within the thin bands are left out of the
+// branch-free loop, flagged, and after the fold decided in FP64 (a warp vote:
+// the whole warp calls this with the same DECIDE).  Sources are read from the
+// global staging.
+template <int T, int KF, bool DECIDE, bool QUASI>
+__device__ __forceinline__ void explicit_image(const float4 *__restrict__ S, const float4 *__restrict__ R,
+                                               const float4 *__restrict__ rdup, const float (&D)[6],
+                                               const WarpSmem<T, KF> &W, const int ti0, const bool act,
+                                               const DecideCtx &dc, const float cut2, const float halfL,
+                                               const float L, float2 (&hx)[KF / 2], float2 (&hy)[KF / 2],
+                                               float2 (&hz)[KF / 2], float2 (&cx)[KF / 2], float2 (&cy)[KF / 2],
+                                               float2 (&cz)[KF / 2]) {
+    constexpr int NPAIR = KF / 2;
+    float2 nxs[NPAIR], nys[NPAIR], nzs[NPAIR], nrx[NPAIR], nry[NPAIR], nrz[NPAIR];
+#pragma unroll
+    for (int q = 0; q < NPAIR; ++q) {
+        float v[2][6];
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+            const int t = 2 * q + e;
+            const int64_t gi = dc.gi0 + t;
+            const float4 r0 = rdup[2 * gi], r1 = rdup[2 * gi + 1];
+            float err;
+            v[e][0] = -two_sum(W.tx[ti0 + t], D[0], err);
+            v[e][3] = -((r0.x + D[3]) + err);
+            v[e][1] = -two_sum(W.ty[ti0 + t], D[1], err);
+            v[e][4] = -((r0.z + D[4]) + err);
+            v[e][2] = -two_sum(W.tz[ti0 + t], D[2], err);
+            v[e][5] = -((r1.x + D[5]) + err);
+        }
+        nxs[q] = make_float2(v[0][0], v[1][0]);
+        nys[q] = make_float2(v[0][1], v[1][1]);
+        nzs[q] = make_float2(v[0][2], v[1][2]);
+        nrx[q] = make_float2(v[0][3], v[1][3]);
+        nry[q] = make_float2(v[0][4], v[1][4]);
+        nrz[q] = make_float2(v[0][5], v[1][5]);
+    }
+    const float band = QUASI ? kFaceBand * L : kCutBand * cut2;
+    const float2 lim = QUASI ? make_float2(-halfL, -halfL) : make_float2(-cut2, -cut2);
+#pragma unroll 1
+    for (int f0 = 0; f0 < T; f0 += kFoldExplicit) {
+        float2 px[NPAIR], py[NPAIR], pz[NPAIR];
+#pragma unroll
+        for (int q = 0; q < NPAIR; ++q) px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+        bool amb = false;
+#pragma unroll 2
+        for (int j = f0; j < f0 + kFoldExplicit; ++j) {
+            const float4 A = S[2 * j], B = S[2 * j + 1];
+            const float4 RA = R[2 * j], RB = R[2 * j + 1];
+            const float2 mj = make_float2(B.z, B.w);
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                const float2 dx = __fadd2_rn(__fadd2_rn(make_float2(A.x, A.y), nxs[q]),
+                                             __fadd2_rn(make_float2(RA.x, RA.y), nrx[q]));
+                const float2 dy = __fadd2_rn(__fadd2_rn(make_float2(A.z, A.w), nys[q]),
+                                             __fadd2_rn(make_float2(RA.z, RA.w), nry[q]));
+                const float2 dz = __fadd2_rn(__fadd2_rn(make_float2(B.x, B.y), nzs[q]),
+                                             __fadd2_rn(make_float2(RB.x, RB.y), nrz[q]));
+                float2 r2 = __fmul2_rn(dx, dx);
+                r2 = __ffma2_rn(dy, dy, r2);
+                r2 = __ffma2_rn(dz, dz, r2);
+                float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                if (DECIDE) {
+                    float2 u;  // signed distance from the boundary: r^2 - (2.6 L)^2, or max_c |d_c| - L/2
+                    if (QUASI)
+                        u = __fadd2_rn(make_float2(fmaxf(fabsf(dx.x), fmaxf(fabsf(dy.x), fabsf(dz.x))),
+                                                   fmaxf(fabsf(dx.y), fmaxf(fabsf(dy.y), fabsf(dz.y)))),
+                                       lim);
+                    else
+                        u = __fadd2_rn(r2, lim);
+                    amb = amb | (fabsf(u.x) < band) | (fabsf(u.y) < band);
+                    ri.x = u.x <= -band ? ri.x : 0.f;
+                    ri.y = u.y <= -band ? ri.y : 0.f;
+                }
+                const float2 sc = __fmul2_rn(__fmul2_rn(mj, ri), __fmul2_rn(ri, ri));
+                px[q] = __ffma2_rn(sc, dx, px[q]);
+                py[q] = __ffma2_rn(sc, dy, py[q]);
+                pz[q] = __ffma2_rn(sc, dz, pz[q]);
+            }
+        }
+        if (DECIDE && __any_sync(0xffffffffu, amb) && amb) {
+            // the band terms of this fold, decided in FP64
+            for (int j = f0; j < f0 + kFoldExplicit; ++j) {
+                const float4 A = S[2 * j], B = S[2 * j + 1];
+                const float4 RA = R[2 * j], RB = R[2 * j + 1];
+                const int64_t gj = dc.gj0 + j;
+#pragma unroll
+                for (int q = 0; q < NPAIR; ++q) {
+#pragma unroll
+                    for (int e = 0; e < 2; ++e) {
+                        const float dx = (e ? (A.y + nxs[q].y) : (A.x + nxs[q].x)) +
+                                         (e ? (RA.y + nrx[q].y) : (RA.x + nrx[q].x));
+                        const float dy = (e ? (A.w + nys[q].y) : (A.z + nys[q].x)) +
+                                         (e ? (RA.w + nry[q].y) : (RA.z + nry[q].x));
+                        const float dz = (e ? (B.y + nzs[q].y) : (B.x + nzs[q].x)) +
+                                         (e ? (RB.y + nrz[q].y) : (RB.x + nrz[q].x));
+                        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                        const float u = QUASI ? fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))) + lim.x : r2 + lim.x;
+                        const int64_t gi = dc.gi0 + 2 * q + e;
+                        if (fabsf(u) < band && gi < dc.n && gj < dc.n &&
+                            include_f64(dc.x[gi], dc.y[gi], dc.z[gi], dc.x[gj], dc.y[gj], dc.z[gj], dc.nx, dc.ny,
+                                        dc.nz, dc.L, dc.images)) {
+                            const float ri = rsqrt_approx(r2);
+                            const float sc = B.z * ri * (ri * ri);
+                            if (e) {
+                                px[q].y = fmaf(sc, dx, px[q].y);
+                                py[q].y = fmaf(sc, dy, py[q].y);
+                                pz[q].y = fmaf(sc, dz, pz[q].y);
+                            } else {
+                                px[q].x = fmaf(sc, dx, px[q].x);
+                                py[q].x = fmaf(sc, dy, py[q].x);
+                                pz[q].x = fmaf(sc, dz, pz[q].x);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+        if (act) {
+#pragma unroll
+            for (int q = 0; q < NPAIR; ++q) {
+                kahan2(hx[q], cx[q], px[q]);
+                kahan2(hy[q], cy[q], py[q]);
+                kahan2(hz[q], cz[q], pz[q]);
+            }
+        }
+    }
+}
+
 // The shift of image k for this tile pair: FP32 values and remainders.
 __device__ __forceinline__ void image_shift(const float *dh, const float *dl, int nx, int ny, int nz,
                                             float (&D)[6]) {
@@ -434,10 +576,10 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
         const float hs = __fadd_rn(ci.w, cj.w) * up;
         const float ext = (eIn + sqrtf(ej.x * ej.x + ej.y * ej.y + ej.z * ej.z)) * up;
         const bool self_tile = (I == J);
-        int nF = 0, nC = 0, nE = 0;
+        int nF = 0, nC = 0, nE = 0, nX = 0;
         for (int k0 = 0; k0 < nimg; k0 += 32) {
             const int k = k0 + lane;
-            int cls = 0;  // 0 none, 1 far inside, 2 far straddling the cut, 3 near
+            int cls = 0;  // 0 none, 1 far inside, 2 far straddling the cut, 3 near, 4 explicit
             bool allin = false;
             if (k < nimg) {
                 int nx, ny, nz;
@@ -458,24 +600,33 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
                 if (cand) {
                     const float dist2 = sx * sx + sy * sy + sz * sz;
                     const float scale = sqrtf(dist2) + ext;
-                    const bool near =
-                        self_tile || gap2 <= hs * hs || ext * ext > dist2 * dn || gap2 < kAlpha2 * scale * scale;
-                    cls = near ? 3 : (allin ? 1 : (a.images == 1 ? 3 : 2));
+                    const bool soft = self_tile || gap2 <= hs * hs;
+                    const bool expansion = ext * ext <= dist2 * dn && gap2 >= kAlpha2 * scale * scale;
+                    if (soft)
+                        cls = 3;
+                    else if (!expansion || (a.images == 1 && !allin))
+                        cls = 4;
+                    else
+                        cls = allin ? 1 : 2;
                 }
             }
             const unsigned lt = (1u << lane) - 1u;
             const unsigned bF = __ballot_sync(0xffffffffu, cls == 1);
             const unsigned bC = __ballot_sync(0xffffffffu, cls == 2);
             const unsigned bE = __ballot_sync(0xffffffffu, cls == 3);
+            const unsigned bX = __ballot_sync(0xffffffffu, cls == 4);
             if (cls == 1)
                 W.lf[nF + __popc(bF & lt)] = (uint16_t)k;
             else if (cls == 2)
                 W.lc[nC + __popc(bC & lt)] = (uint16_t)k;
             else if (cls == 3)
                 W.le[nE + __popc(bE & lt)] = (uint16_t)(k | (allin ? kAllIn : 0));
+            else if (cls == 4)
+                W.lx[nX + __popc(bX & lt)] = (uint16_t)(k | (allin ? kAllIn : 0));
             nF += __popc(bF);
             nC += __popc(bC);
             nE += __popc(bE);
+            nX += __popc(bX);
         }
         __syncwarp();
 
@@ -502,6 +653,25 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
             far_image<T, NPAIR, true>(W, D, ti0, act, dc, hx, hy, hz, cx, cy, cz);
         }
         const float4 *S = a.jdup + 2 * J * T, *R = a.rdup + 2 * J * T;
+        for (int b = 0; b < nX; b += IPW) {
+            const bool act = b + g < nX;
+            const int code = W.lx[act ? b + g : b];
+            float D[6];
+            image_of(code & 0x1ff, a.images, dc.nx, dc.ny, dc.nz);
+            image_shift(W.dh, W.dl, dc.nx, dc.ny, dc.nz, D);
+            // one choice for the whole warp (the image slots may differ): the
+            // deciding loop votes across the warp after each fold
+            const bool decide = __any_sync(0xffffffffu, !(code & kAllIn));
+            if (!decide)
+                explicit_image<T, KF, false, false>(S, R, a.rdup, D, W, ti0, act, dc, cut2, halfL, L, hx, hy, hz, cx,
+                                                    cy, cz);
+            else if (a.images == 1)
+                explicit_image<T, KF, true, true>(S, R, a.rdup, D, W, ti0, act, dc, cut2, halfL, L, hx, hy, hz, cx,
+                                                  cy, cz);
+            else
+                explicit_image<T, KF, true, false>(S, R, a.rdup, D, W, ti0, act, dc, cut2, halfL, L, hx, hy, hz, cx,
+                                                   cy, cz);
+        }
         for (int b = 0; b < nE; b += IPW) {
             const bool act = b + g < nE;
             const int code = W.le[act ? b + g : b];

@@ -111,6 +111,29 @@ def test_periodic_16k_sampled_targets(kind):
     assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
 
 
+@pytest.mark.parametrize("images", [0, 1])
+@pytest.mark.parametrize("n", [1, 2, 63, 65])
+def test_periodic_small_and_ragged(images, n):
+    """Degenerate and ragged sizes: one particle (no pair; its own images are
+    excluded, so no force), two particles, and tile counts one below and above
+    a 64-particle tile."""
+    L = 1.5
+    rng = np.random.default_rng(70 + n + images)
+    pos = rng.random((n, 3)) * L
+    m = rng.uniform(0.5, 1.5, n)
+    h = rng.uniform(0.002, 0.01, n) * L
+    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images)
+    for prec in (steps.STEPS_F64, steps.STEPS_F32_COMP):
+        sim = periodic_sim(pos, m, h, L, images, prec)
+        got = sim.forces()
+        sim.close()
+        if n == 1:
+            assert np.all(got == 0.0) and np.all(ref == 0.0)
+            continue
+        e = rel_err(got, ref)
+        assert e.max() <= (1e-12 if prec == steps.STEPS_F64 else MAX_TOL), (prec, e.max())
+
+
 def test_pairs_on_the_cut_sphere():
     """Pairs whose separation puts one image within ~1e-8 of 2.6 L, on both sides:
     the FP32 path must make the definition's FP64 decision for every one."""
