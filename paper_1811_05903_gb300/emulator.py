@@ -5,8 +5,8 @@ library's kernels -> error on held-out plain simulations.
 The simulations are run for the statistics of the density field (Sec. 1;
 opening of Sec. 3).  The emulator answers "what xi(r) would a run at these
 cosmological parameters give" in microseconds instead of a simulation, which
-is what a parameter fit needs; the plain batched simulation stays the judge of
-its error.  Every numerical step runs in libsteps: the N-body runs
+is what a parameter fit needs; the plain batched simulation remains the
+measure of its error.  Every numerical step runs in libsteps: the N-body runs
 (steps_ensemble_*), the pair counts (steps_paircount) and the network's
 training and inference (steps_emu_*).  This module marshals: it draws the
 parameter sets and initial conditions (``workloads``), maps features and
