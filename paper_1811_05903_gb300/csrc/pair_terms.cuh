@@ -74,9 +74,11 @@ __device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
 // The terms of one near tile pair for this lane's KI targets (KI/2 packed
 // pairs), folded into the targets' sums every FOLD sources.  Each source is
 // read once from shared memory for all pairs.  SOFT: some pair may lie inside
-// h_i + h_j (or the tile pair is a tile with itself): per source the warp
-// checks and takes the full spline of Eq. 4 where needed, and self pairs
-// (d == 0) add nothing; otherwise every pair is Newtonian and d != 0.
+// h_i + h_j (or the tile pair is a tile with itself): the packed loop leaves
+// every pair with r^2 <= (h_i + h_j)^2 out (self pairs, r = 0, among them) and
+// flags the lane; after the fold the flagged lanes add those pairs with the
+// spline of Eq. 4 (a warp vote: the whole warp calls this with the same SOFT).
+// Otherwise every pair is Newtonian and d != 0.
 template <int KI, bool COMP, int FOLD, bool SOFT>
 __device__ __forceinline__ void near_tile_terms(
     const float4 *__restrict__ S, const float4 *__restrict__ Rr, const float2 (&nxs)[KI / 2],
@@ -99,6 +101,7 @@ __device__ __forceinline__ void near_tile_terms(
                 pz[q] = hz[q];
             }
         }
+        bool inner = false;  // this lane left a pair inside the softening out of the packed sum
 #pragma unroll 2
         for (int j = f0; j < f0 + FOLD; ++j) {
             const float4 A = S[2 * j], B = S[2 * j + 1];
@@ -114,44 +117,52 @@ __device__ __forceinline__ void near_tile_terms(
                 float2 r2 = __fmul2_rn(dx, dx);
                 r2 = __ffma2_rn(dy, dy, r2);
                 r2 = __ffma2_rn(dz, dz, r2);
-                if (!SOFT) {
-                    const float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
-                    const float2 ri2 = __fmul2_rn(ri, ri);
-                    const float2 sc = __fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ri), ri2);
-                    px[q] = __ffma2_rn(sc, dx, px[q]);
-                    py[q] = __ffma2_rn(sc, dy, py[q]);
-                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
-                    continue;
+                float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                if (SOFT) {
+                    const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
+                    const float2 H2 = __fmul2_rn(H, H);
+                    const bool ix = r2.x <= H2.x, iy = r2.y <= H2.y;
+                    inner = inner | ix | iy;
+                    ri.x = ix ? 0.f : ri.x;
+                    ri.y = iy ? 0.f : ri.y;
                 }
-                const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
-                const float2 H2 = __fmul2_rn(H, H);
-                const bool inner = r2.x < H2.x || r2.y < H2.y;
-                if (!__any_sync(0xffffffffu, inner)) {
-                    const float2 ri = make_float2(r2.x > 0.f ? rsqrt_approx(r2.x) : 0.f,
-                                                  r2.y > 0.f ? rsqrt_approx(r2.y) : 0.f);
-                    const float2 ri2 = __fmul2_rn(ri, ri);
-                    float2 sc = __fmul2_rn(make_float2(B.z, B.w), ri);
-                    sc = __fmul2_rn(sc, ri2);
-                    px[q] = __ffma2_rn(sc, dx, px[q]);
-                    py[q] = __ffma2_rn(sc, dy, py[q]);
-                    pz[q] = __ffma2_rn(sc, dz, pz[q]);
-                } else {
+                const float2 ri2 = __fmul2_rn(ri, ri);
+                const float2 sc = __fmul2_rn(__fmul2_rn(make_float2(B.z, B.w), ri), ri2);
+                px[q] = __ffma2_rn(sc, dx, px[q]);
+                py[q] = __ffma2_rn(sc, dy, py[q]);
+                pz[q] = __ffma2_rn(sc, dz, pz[q]);
+            }
+        }
+        if (SOFT && __any_sync(0xffffffffu, inner) && inner) {
+            // the pairs inside h_i + h_j of this fold, with the same FP32 separations
+            for (int j = f0; j < f0 + FOLD; ++j) {
+                const float4 A = S[2 * j], B = S[2 * j + 1];
+                const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
+#pragma unroll
+                for (int q = 0; q < NPAIR; ++q) {
 #pragma unroll
                     for (int e = 0; e < 2; ++e) {
-                        const float r2e = e ? r2.y : r2.x;
-                        if (r2e > 0.f) {
-                            const float He = e ? H.y : H.x;
-                            const float ri = rsqrt_approx(r2e);
-                            const float g = (r2e >= He * He) ? ri * ri * ri : spline_over_r_f32(r2e * ri, He);
-                            const float sc = B.z * g;
+                        const float dx = __fadd_rn(__fadd_rn(e ? A.y : A.x, e ? nxs[q].y : nxs[q].x),
+                                                   __fadd_rn(e ? RA.y : RA.x, e ? nrx[q].y : nrx[q].x));
+                        const float dy = __fadd_rn(__fadd_rn(e ? A.w : A.z, e ? nys[q].y : nys[q].x),
+                                                   __fadd_rn(e ? RA.w : RA.z, e ? nry[q].y : nry[q].x));
+                        const float dz = __fadd_rn(__fadd_rn(e ? B.y : B.x, e ? nzs[q].y : nzs[q].x),
+                                                   __fadd_rn(e ? RB.y : RB.x, e ? nrz[q].y : nrz[q].x));
+                        const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
+                        const float H = __fadd_rn(e ? hI[q].y : hI[q].x, e ? RB.w : RB.z);
+                        const float H2 = __fmul_rn(H, H);
+                        if (r2 <= H2 && r2 > 0.f) {
+                            const float ri = rsqrt_approx(r2);
+                            const float g = (r2 >= H2) ? ri * ri * ri : spline_over_r_f32(r2 * ri, H);
+                            const float sc = (e ? B.w : B.z) * g;
                             if (e) {
-                                px[q].y = fmaf(sc, dx.y, px[q].y);
-                                py[q].y = fmaf(sc, dy.y, py[q].y);
-                                pz[q].y = fmaf(sc, dz.y, pz[q].y);
+                                px[q].y = fmaf(sc, dx, px[q].y);
+                                py[q].y = fmaf(sc, dy, py[q].y);
+                                pz[q].y = fmaf(sc, dz, pz[q].y);
                             } else {
-                                px[q].x = fmaf(sc, dx.x, px[q].x);
-                                py[q].x = fmaf(sc, dy.x, py[q].x);
-                                pz[q].x = fmaf(sc, dz.x, pz[q].x);
+                                px[q].x = fmaf(sc, dx, px[q].x);
+                                py[q].x = fmaf(sc, dy, py[q].x);
+                                pz[q].x = fmaf(sc, dz, pz[q].x);
                             }
                         }
                     }
