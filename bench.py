@@ -455,16 +455,22 @@ def main():
     ap.add_argument("--no-periodic", action="store_true")
     ap.add_argument("--periodic-only", action="store_true",
                     help="time only the periodic-mode force evaluations (one JSON line; not the bench line)")
+    ap.add_argument("--ensemble-only", action="store_true",
+                    help="time only the batched ensemble against its members run one by one (one JSON line; "
+                         "not the bench line)")
     args = ap.parse_args()
-    if args.periodic_only:
+    if args.periodic_only or args.ensemble_only:
         import torch
 
         import paper_1811_05903_gb300.build as libbuild
-        from paper_1811_05903_gb300 import steps
+        from paper_1811_05903_gb300 import steps, workloads
         torch.cuda.set_device(0)
         libbuild.build()
         steps.load()
-        print(json.dumps({"periodic": periodic_throughput(steps)}))
+        if args.periodic_only:
+            print(json.dumps({"periodic": periodic_throughput(steps)}))
+        else:
+            print(json.dumps({"ensemble": ensemble_throughput(torch.cuda.Stream(), steps, workloads)}))
     elif args.impl == "reference":
         run_reference(args)
     else:
