@@ -176,12 +176,14 @@ steps_status sync_and_check(steps_ctx *c) {
 // Default variant before tuning (and the choice below 2^17 particles): the
 // first built variant of the requested summation mode with 4 targets per
 // thread; systems below 32,768 particles use 64-particle tiles (2 targets per
-// thread) to limit padding and near-field work.
+// thread) to limit padding and near-field work.  Periodic mode always stages
+// 64-particle tiles: smaller tiles leave fewer images straddling the cut
+// sphere (measured 3% faster than 128 at 65,536 and 131,072 particles).
 int pick_variant(const steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
     if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())
         return c->cfg.tile_override - 1;
-    const int ki = c->n >= 32768 ? 4 : 2;
+    const int ki = (c->n >= 32768 && !c->cosmo.periodic) ? 4 : 2;
     for (int k = 0; k < num_variants(); ++k) {
         const Variant &v = variant(k);
         if (v.comp == comp && v.KI == ki) return k;
