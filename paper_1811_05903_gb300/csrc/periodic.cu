@@ -570,7 +570,7 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
             const float kc = W.sf[4 * j + 1].z * cut2;
             W.sk[j] = make_float4(-kc, -kc, kCutBand * kc, kCutBand * kc);
         }
-        // sort the candidate images of this tile pair into the three lists
+        // sort the candidate images of this tile pair into the four lists
         const float wx = __fadd_rn(ei.x, ej.x) * up + mg, wy = __fadd_rn(ei.y, ej.y) * up + mg,
                     wz = __fadd_rn(ei.z, ej.z) * up + mg;
         const float hs = __fadd_rn(ci.w, cj.w) * up;
