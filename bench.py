@@ -233,6 +233,9 @@ def periodic_throughput(steps_mod, n=16384, L=1.0, seed=21):
     around the force kernels.  Work counted as N^2 x (4 pi / 3) 2.6^3 pair-image
     terms for the cut sum (the expected number of images inside the cut sphere)
     and N^2 for the quasi-periodic sum."""
+    import torch
+    props = torch.cuda.get_device_properties(torch.cuda.current_device())
+    peak = fp32_peak_tflops(props.multi_processor_count, float(peaks().get("sm_max_mhz", 2070.0)))
     rng = np.random.default_rng(seed)
     pos = rng.random((n, 3)) * L
     m = np.full(n, 1.0 / n)
@@ -250,8 +253,9 @@ def periodic_throughput(steps_mod, n=16384, L=1.0, seed=21):
         ms, launches, _ = steps_mod.steps_profile_read(sim.ctx, reset=True)
         sim.close()
         per = ms * 1e-3 / max(launches, 1)
+        tflops = 20 * terms * n * n / per / 1e12
         out[name] = {"ms_per_evaluation": 1e3 * per, "pair_image_terms_per_s": terms * n * n / per,
-                     "fp32_tflops_at_20_flop": 20 * terms * n * n / per / 1e12}
+                     "fp32_tflops_at_20_flop": tflops, "frac_of_fp32_peak": tflops / peak}
     return out
 
 
