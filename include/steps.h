@@ -73,7 +73,8 @@ typedef struct {
     int mode;                 /* steps_mode */
     int prec;                 /* steps_prec */
     int resort_every;         /* re-sort particles spatially every this many steps (<=0: default 8) */
-    int tile_override;        /* 0 = autotuned force-kernel variant; k>0 selects variant k-1 */
+    int tile_override;        /* 0 = autotuned force-kernel variant (STEPS_PERIODIC: 64-particle tiles,
+                                 not tuned); k>0 selects variant k-1 (its tile size in periodic mode) */
     double box;               /* STEPS_PERIODIC: side L of the periodic box */
     int images;               /* STEPS_PERIODIC: 0 = image sum cut at 2.6 L (Eq. 5), 1 = quasi-periodic */
 } steps_config;
