@@ -170,7 +170,7 @@ __device__ __forceinline__ void far_image(const WarpSmem<T, 2 * NPAIR> &W, const
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) px[q] = py[q] = pz[q] = p0[q] = make_float2(0.f, 0.f);
         bool amb = false;  // some term of this lane lies in the band around the cut
-#pragma unroll 4
+#pragma unroll 8
         for (int j = j0; j < j0 + kFoldFar; ++j) {
             const float4 A = W.sf[4 * j], B = W.sf[4 * j + 1], C = W.sf[4 * j + 2], E = W.sf[4 * j + 3];
             const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
