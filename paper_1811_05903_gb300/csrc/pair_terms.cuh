@@ -102,7 +102,7 @@ __device__ __forceinline__ void near_tile_terms(
             }
         }
         bool inner = false;  // this lane left a pair inside the softening out of the packed sum
-#pragma unroll 2
+#pragma unroll 4
         for (int j = f0; j < f0 + FOLD; ++j) {
             const float4 A = S[2 * j], B = S[2 * j + 1];
             const float4 RA = Rr[2 * j], RB = Rr[2 * j + 1];
