@@ -30,8 +30,8 @@
 // Each warp owns one target tile and a chunk of source tiles (a work item);
 // lanes are grouped into image slots so that one warp runs 32 / (T / KF)
 // images at once with KF targets per lane and the source loads are shared
-// (broadcast) by all slots.  FP32 partial sums are Kahan-folded every 32 (far)
-// or 8 (near) sources, added into FP64 per source tile, combined across the
+// (broadcast) by all slots.  FP32 partial sums are Kahan-folded every 32 (far),
+// 16 (explicit) or 8 (near) sources, added into FP64 per source tile, combined across the
 // slots in a fixed order and written per work item; the reduction kernel adds
 // the items in order: deterministic.
 //
