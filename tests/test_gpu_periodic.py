@@ -134,6 +134,22 @@ def test_periodic_small_and_ragged(images, n):
         assert e.max() <= (1e-12 if prec == steps.STEPS_F64 else MAX_TOL), (prec, e.max())
 
 
+@pytest.mark.parametrize("images", [0, 1])
+def test_periodic_65k_sampled_targets(images):
+    """N = 65,536 (1,024 tiles, 19 source chunks per target tile): FP32 against
+    the oracle on 32 sampled targets of a clumpy box."""
+    L, n = 1.0, 65536
+    pos, m, h = clumpy_box(65, n, L)
+    tg = np.sort(np.random.default_rng(66).choice(n, 32, replace=False))
+    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images, targets=tg)
+    sim = periodic_sim(pos, m, h, L, images, steps.STEPS_F32_COMP)
+    e = rel_err(sim.forces()[tg], ref)
+    sim.close()
+    rms = math.sqrt(np.mean(e ** 2))
+    print("N=65536 images=%d FP32 rms %.2e max %.2e" % (images, rms, e.max()))
+    assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
+
+
 def test_pairs_on_the_cut_sphere():
     """Pairs whose separation puts one image within ~1e-8 of 2.6 L, on both sides:
     the FP32 path must make the definition's FP64 decision for every one."""
