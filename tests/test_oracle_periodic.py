@@ -124,3 +124,19 @@ def test_periodic_kdk_wraps_and_conserves_momentum():
     # the pair term conserves momentum; the friction term scales it by the same factor for every particle
     p = (m[:, None] * kd.vel).sum(0)
     assert np.abs(p).max() < 1e-12 * (m[:, None] * np.abs(kd.vel)).sum()
+
+
+@pytest.mark.parametrize("images", [0, 1])
+def test_target_subset_equals_full_rows(images):
+    """The sampled-target form used at large N returns exactly the rows of the
+    full evaluation (same loops, same order)."""
+    rng = np.random.default_rng(6)
+    L, n = 1.5, 150
+    pos = rng.random((n, 3)) * L
+    m = rng.uniform(0.5, 2.0, n)
+    h = rng.uniform(0.01, 0.05, n)
+    full = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images)
+    tg = np.array([0, 7, 33, 149, 7])
+    sub = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images, targets=tg)
+    assert np.array_equal(sub, full[tg])
+
