@@ -7,7 +7,9 @@ compensated sums, FP64 integrator.  One step = one full kick-drift-kick step
 (kick, drift, RK4 a(t), staging, pair-force kernel, fixup, kick; spatial
 re-sort every 8 steps), i.e. N^2 pair interactions.
 
-Prints one JSON line.  --impl reference times the FP64 CPU oracle instead.
+Prints one JSON line.  --impl reference times the FP64 CPU oracle instead;
+--ensemble-only and --periodic-only time the batched ensemble or the
+periodic-mode force evaluations alone (their own JSON line, not the bench line).
 Multi-GPU (torchrun): the path does not shard; each rank runs an independent
 replica and the job value is the sum of all ranks' interactions over the
 slowest rank's time.
