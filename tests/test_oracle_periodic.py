@@ -140,3 +140,36 @@ def test_target_subset_equals_full_rows(images):
     sub = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images, targets=tg)
     assert np.array_equal(sub, full[tg])
 
+
+@pytest.mark.parametrize("images", [0, 1])
+def test_brute_force_newtonian_image_sum(images):
+    """Tiny softening (every pair Newtonian): the oracle equals a direct Python
+    sum of G m_j d / |d|^3 over the images the definition keeps, enumerated
+    over a wide cube of n."""
+    rng = np.random.default_rng(12)
+    L, n, G = 1.3, 6, 0.8
+    pos = rng.random((n, 3)) * L
+    m = rng.uniform(0.5, 2.0, n)
+    h = np.full(n, 1e-6)
+    got = oracle.pair_acc_periodic(pos, m, h, G, L, images)
+    rng4 = range(-4, 5)
+    want = np.zeros((n, 3))
+    for i in range(n):
+        for j in range(n):
+            if j == i:
+                continue
+            d0 = pos[i] - pos[j]
+            if images == 1:
+                nv = np.floor(d0 / L + 0.5)
+                d = d0 - nv * L
+                want[i] -= G * m[j] * d / np.linalg.norm(d) ** 3
+                continue
+            for a in rng4:
+                for b in rng4:
+                    for c in rng4:
+                        d = d0 - np.array([a, b, c]) * L
+                        r = np.linalg.norm(d)
+                        if r < 2.6 * L:
+                            want[i] -= G * m[j] * d / r ** 3
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-12 * np.abs(want).max())
+
