@@ -88,6 +88,8 @@ struct steps_ctx {
     // FP32 staging
     Staging stg;
     float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *fdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
+    float4 *sdup_buf = nullptr;           // symmetric-kernel layout
+    unsigned long long *qmax = nullptr;   // largest |coordinate| (centre grid of the staging)
     NearScratch nr;                       // near-field bitmap and work items
     double *per_part = nullptr;           // periodic mode: FP64 partials per work item
     SimDesc *dsim = nullptr;              // device table of one system
@@ -101,6 +103,7 @@ struct steps_ctx {
     SortScratch srt;
     int *err = nullptr;       // device error word
     int *flag = nullptr;      // device validation flags
+    int *nonfinite = nullptr; // device word: a force or state value was NaN or Inf (err + 2)
     long long wait_ns = 2000000000LL;
     int64_t since_sort = 0;
     // benchmark hooks
@@ -163,12 +166,17 @@ void dev_free(steps_ctx *c, void *p) {
 // Check the device error word and clear it.
 steps_status sync_and_check(steps_ctx *c) {
     STEPS_CUDA(cudaStreamSynchronize(c->st));
-    int e = 0;
-    STEPS_CUDA(cudaMemcpy(&e, c->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (e) {
+    int w[3] = {0, 0, 0};  // error word, validation flags, non-finite word
+    STEPS_CUDA(cudaMemcpy(w, c->err, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w[0]) {
         STEPS_CUDA(cudaMemset(c->err, 0, sizeof(int)));
-        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", e);
-        return (steps_status)e;
+        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", w[0]);
+        return (steps_status)w[0];
+    }
+    if (w[2]) {
+        STEPS_CUDA(cudaMemset(c->nonfinite, 0, sizeof(int)));
+        set_error("a computed force, position or velocity is NaN or Inf (FP32 overflow of the inputs' scale?)");
+        return STEPS_ENONFINITE;
     }
     return STEPS_OK;
 }
@@ -206,6 +214,8 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.jdup = c->jdup_buf;
     c->stg.rdup = c->rdup_buf;
     c->stg.fdup = (v.form == 1 || c->cosmo.periodic) ? c->fdup_buf : nullptr;
+    c->stg.sdup = v.form == 2 ? c->sdup_buf : nullptr;
+    c->stg.qmax = c->qmax;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     SimDesc d{};
@@ -293,6 +303,9 @@ steps_status compute_forces(steps_ctx *c) {
                                 c->az, c->st));
         c->kernel_launches += 6;  // stage, far, near count, near scan, near, fixup
     }
+    // non-finite result check (read at the next synchronising call: STEPS_ENONFINITE)
+    STEPS_CUDA(launch_check_finite3(c->n, c->ax, c->ay, c->az, c->nonfinite, c->st));
+    c->kernel_launches += 1;
     c->force_launches += 1;
     if (prof) c->force_events.push_back({e0, e1});
     if (prof && f0) c->far_events.push_back({f0, f1});
@@ -412,9 +425,10 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     c->nred = 256;
     STEPS_TRY(alloc_n(c, &c->red, 4 * c->nred + 8));
     STEPS_TRY(alloc_n(c, &c->tmp3, 3 * n));
-    STEPS_TRY(alloc_n(c, &c->err, 2));
+    STEPS_TRY(alloc_n(c, &c->err, 4));
     c->flag = c->err + 1;
-    STEPS_CUDA(cudaMemsetAsync(c->err, 0, 2 * sizeof(int), c->st));
+    c->nonfinite = c->err + 2;
+    STEPS_CUDA(cudaMemsetAsync(c->err, 0, 4 * sizeof(int), c->st));
     // staging: padded to the largest multiple any variant's i-block (W x 32 KI
     // targets) needs, so that every variant fits; each pads to its own multiple
     c->np = 0;
@@ -426,6 +440,12 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->jdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->rdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->fdup_buf, 4 * c->np));
+    STEPS_TRY(alloc_n(c, &c->sdup_buf, 2 * c->np));
+    STEPS_TRY(alloc_n(c, &c->qmax, 1));
+    STEPS_TRY(alloc_n(c, &c->nr.sym_acc, 3 * c->np));
+    STEPS_TRY(alloc_n(c, &c->nr.tscale, c->ntile_cap));
+    STEPS_TRY(alloc_n(c, &c->nr.tinv, c->ntile_cap));
+    c->nr.nonfinite = c->nonfinite;
     STEPS_TRY(alloc_n(c, &c->nr.bits, (size_t)c->ntile_cap * ((c->ntile_cap + 31) / 32)));
     STEPS_TRY(alloc_n(c, &c->nr.cnt, c->ntile_cap));
     STEPS_TRY(alloc_n(c, &c->nr.item_off, c->ntile_cap + 1));
@@ -782,6 +802,8 @@ steps_status steps_get_state(steps_ctx *c, double *pos, double *vel, double *acc
         set_error("ctx is NULL");
         return STEPS_EINVAL;
     }
+    STEPS_CUDA(launch_check_finite3(c->n, c->x, c->y, c->z, c->nonfinite, c->st));
+    STEPS_CUDA(launch_check_finite3(c->n, c->vx, c->vy, c->vz, c->nonfinite, c->st));
     if (pos) {
         STEPS_TRY(store3(c, pos, c->x, c->y, c->z));
         STEPS_CUDA(cudaStreamSynchronize(c->st));

@@ -42,101 +42,14 @@
 #include <algorithm>
 #include <vector>
 
+#include "async_copy.cuh"
 #include "pair_terms.cuh"
+#include "systems.cuh"
 #include "steps_internal.h"
 
 namespace steps {
 
 namespace {
-
-constexpr long long kDrainNs = 2000000000LL;  // bound for draining in-flight copies
-
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(bar), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns() {
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// Wait for phase `parity` of an mbarrier to complete, giving up after
-// limit_ns nanoseconds (limit_ns == 0: give up at once; used by tests).
-__device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit_ns) {
-    if (limit_ns == 0) return false;
-    if (mbar_try_wait(bar, parity)) return true;
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-#pragma unroll 1
-        for (int i = 0; i < 16; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
-        if ((long long)(global_ns() - t0) > limit_ns) return false;
-    }
-}
-
-__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void *src, uint32_t bytes,
-                                         uint32_t bar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-            dst),
-        "l"(src), "r"(bytes), "r"(bar)
-        : "memory");
-}
-
-// Tile-pair classification (done once per pair by the far-field producer;
-// the near-field kernel reads the resulting bitmap).  Conservative margins of
-// 2^-18 cover the FP32 rounding of the box arithmetic.
-//  * near if some pair may be closer than h_i + h_j (spline branches of Eq. 4);
-//  * near if the boxes are closer than alpha x (|c_I - c_J| + |e_I| + |e_J|),
-//    where one FP32 difference of offsets could lose relative precision in d;
-//  * near if |e_I| + |e_J| > |c_I - c_J|: the far field's first-order
-//    correction of the target shift uses the source tile's monopole tidal
-//    tensor, which needs the tiles to be smaller than their distance.
-__device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei, const float4 cj,
-                                               const float4 ej, const float alpha2) {
-    const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
-    const float dcx = __fsub_rn(ci.x, cj.x), dcy = __fsub_rn(ci.y, cj.y), dcz = __fsub_rn(ci.z, cj.z);
-    const float gx = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcx), dn), __fmul_rn(__fadd_rn(ei.x, ej.x), up)));
-    const float gy = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcy), dn), __fmul_rn(__fadd_rn(ei.y, ej.y), up)));
-    const float gz = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcz), dn), __fmul_rn(__fadd_rn(ei.z, ej.z), up)));
-    const float gap2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
-    const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
-    if (gap2 <= __fmul_rn(hs, hs)) return true;
-    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dcx, dcx), __fmul_rn(dcy, dcy)), __fmul_rn(dcz, dcz));
-    const float ni = __fadd_rn(__fadd_rn(__fmul_rn(ei.x, ei.x), __fmul_rn(ei.y, ei.y)), __fmul_rn(ei.z, ei.z));
-    const float nj = __fadd_rn(__fadd_rn(__fmul_rn(ej.x, ej.x), __fmul_rn(ej.y, ej.y)), __fmul_rn(ej.z, ej.z));
-    const float dist = __fsqrt_rn(n2);
-    const float ext = __fadd_rn(__fsqrt_rn(ni), __fsqrt_rn(nj));
-    if (__fmul_rn(ext, up) > dist) return true;
-    const float scale = __fadd_rn(dist, ext);
-    return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
-}
 
 // Far tile pair by expansion about the source tile's centre (EXP variants).
 // With s = fl(o_i + (c_I - c_J)) the target relative to the source tile's
@@ -280,26 +193,6 @@ struct ForceArgs {
     float alpha2;                      // near-field criterion, squared
     long long wait_ns;
 };
-
-// System holding stream-K unit u (last table entry whose unit_off <= u).
-__device__ __forceinline__ int sim_of_unit(const SimDesc *__restrict__ sims, int nsims, int64_t u) {
-    int lo = 0, hi = nsims;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (sims[mid].unit_off <= u) lo = mid; else hi = mid;
-    }
-    return lo;
-}
-
-// System holding global tile r.
-__device__ __forceinline__ int sim_of_tile(const SimDesc *__restrict__ sims, int nsims, int64_t r) {
-    int lo = 0, hi = nsims;
-    while (hi - lo > 1) {
-        const int mid = (lo + hi) >> 1;
-        if (sims[mid].tile_off <= r) lo = mid; else hi = mid;
-    }
-    return lo;
-}
 
 // Far field of the pair term over this CTA's stream-K range of tile pairs.
 //   KI    targets per thread (KI/2 packed pairs), T = 32 KI particles per tile
@@ -1004,6 +897,8 @@ const VariantImpl kVariants[] = {
     STEPS_VARIANT(4, 4, 4, false, 32, 3, 4, false, false, "naive_ki4_w4_u4"),
     STEPS_VARIANT(4, 8, 4, false, 32, 2, 2, false, false, "naive_ki4_w8_u2"),
     STEPS_VARIANT(2, 8, 4, false, 32, 4, 4, false, false, "naive_ki2_w8_u4"),
+    // symmetric far field (force_sym.cu): 256-particle tiles, 4 compute warps
+    {{8, 4, 2, true, "sym_ki8_w4", 2}, nullptr, near_f32_kernel<8, true, kNearFold>, 0, near_smem_of<8>()},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -1011,7 +906,9 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
 int num_variants() { return kNumVariants; }
 const Variant &variant(int k) { return kVariants[k].v; }
-size_t force_smem_bytes(int k) { return kVariants[k].smem; }
+size_t force_smem_bytes(int k) {
+    return kVariants[k].v.form == 2 ? sym_smem_bytes(kVariants[k].v.W, kVariants[k].v.NS) : kVariants[k].smem;
+}
 
 ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const SimDesc *dev_sims,
                            int64_t *bits_words) {
@@ -1023,6 +920,7 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
     p.sims = dev_sims;
     p.nsims = nsims;
     int64_t units = 0, blocks = 0, bits = 0;
+    const bool sym = vi.v.form == 2;
     std::vector<int64_t> starts;  // unit at which every target block starts
     for (int s = 0; s < nsims; ++s) {
         SimDesc &d = descs[s];
@@ -1030,17 +928,27 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
         d.blk_off = blocks;
         d.words = (d.ntile + 31) / 32;
         d.bits_off = bits;
-        for (int64_t b = 0; b < d.ntile / W; ++b) starts.push_back(units + b * d.ntile);
-        units += (d.ntile / W) * d.ntile;
+        if (!sym)
+            for (int64_t b = 0; b < d.ntile / W; ++b) starts.push_back(units + b * d.ntile);
+        units += sym ? sym_units(d.ntile, W) : (d.ntile / W) * d.ntile;
         blocks += d.ntile / W;
         bits += d.ntile * d.words;
     }
     if (bits_words) *bits_words = bits;
     p.niblk = blocks;
     p.units = units;
+    cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
+    if (sym) {
+        // persistent grid; every unit adds to fixed-point sums, no per-CTA partials
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(W, vi.v.NS),
+                                                                    units));
+        p.grid = (int)grid;
+        p.smax = 0;
+        p.partial_elems = 0;
+        return p;
+    }
     int per_sm = 1;
     cudaFuncSetAttribute(vi.fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.smem);
-    cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vi.fn, (vi.v.W + 1) * 32, vi.smem) !=
             cudaSuccess ||
         per_sm < 1)
@@ -1096,11 +1004,22 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.smax = p.smax;
     a.alpha2 = alpha * alpha;
     a.wait_ns = wait_ns;
-    cudaError_t e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)nr.bits_words, st);
-    if (e != cudaSuccess) return e;
-    if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
-    vi.fn<<<p.grid, (vi.v.W + 1) * 32, vi.smem, st>>>(a);
-    if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
+    cudaError_t e;
+    if (vi.v.form == 2) {
+        // classification pass (whole bitmap, fixed-point scales), then the symmetric far field
+        if ((e = cudaMemsetAsync(nr.sym_acc, 0, sizeof(unsigned long long) * 3 * (size_t)s.np, st)) != cudaSuccess)
+            return e;
+        if ((e = launch_sym_classify(s, p, nr, alpha, stats, st)) != cudaSuccess) return e;
+        if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
+        if ((e = launch_sym_far(s, p, nr, err, wait_ns, st)) != cudaSuccess) return e;
+        if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
+    } else {
+        e = cudaMemsetAsync(nr.bits, 0, sizeof(uint32_t) * (size_t)nr.bits_words, st);
+        if (e != cudaSuccess) return e;
+        if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
+        vi.fn<<<p.grid, (vi.v.W + 1) * 32, vi.smem, st>>>(a);
+        if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
+    }
     near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, p.sims, p.nsims,
                                                                              s.ntile, nr.cnt);
     near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, nr.item_off, nr.meta);
@@ -1115,6 +1034,7 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
 cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *partial,
                          const NearScratch &nr, double G, double *ax, double *ay, double *az,
                          cudaStream_t st) {
+    if (kVariants[p.variant].v.form == 2) return launch_sym_fixup(s, p, nr, G, ax, ay, az, st);
     const int tb = 256;
     const int64_t blocks = (s.n + tb - 1) / tb;
     fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(partial, nr.item_part, nr.item_off, p.sims, p.nsims, s.T,

@@ -1,0 +1,556 @@
+// Symmetric FP32 far field of the pair term (Eq. 8; Eq. 3 with the Newtonian
+// branch of Eq. 4) for sm_103a.
+//
+// The pair term is antisymmetric: particle i feels m_j (x_j - x_i)/r^3 and
+// particle j feels m_i (x_i - x_j)/r^3 from the same separation and the same
+// 1/r^3 (Newton's third law).  This kernel evaluates every far pair of tiles
+// (I < J) once and adds the pair's force to both particles: per pair the
+// separation (3), r^2 (3), MUFU rsqrt, 1/r^3 (2), and two scaled
+// accumulations (1 + 3 each) -- 16 FP32 lane operations and one MUFU for two
+// interactions, against 20 and two for evaluating each order separately.
+//
+// Work layout (GB300-first):
+//  * Tiles of T = 256 Morton-ordered particles with FP32 offsets from an FP32
+//    tile centre; the centres are rounded to a grid that makes every
+//    difference of two centres exact in FP32, so a tile pair shares one exact
+//    shift dc = c_I - c_J.
+//  * A unit is (target block b of W tiles, source tile J) with J after the
+//    block; pairs of tiles inside one block go to the near-field kernel.  A
+//    persistent grid splits the units evenly (stream-K); a producer warp
+//    streams source tiles into a shared-memory ring with TMA bulk copies
+//    (cp.async.bulk completing on mbarriers); compute warp w owns target tile
+//    b W + w.
+//  * Inside a warp, lane l holds 8 targets (particles l + 32 t) as 4 packed
+//    pairs (FFMA2).  The source tile is processed in 4 rounds of 32 steps; at
+//    step s lane l takes the 2 sources of group (l + s) mod 32, so no two
+//    lanes touch the same source, and the sources' running sums travel with
+//    the group from lane to lane by one shuffle per step.  After a round each
+//    lane holds the complete contribution of the warp's 256 targets to its own
+//    group's sources.
+//  * Target sums: FP32 partials over 32 sources folded into a per-target
+//    compensated (Kahan) pair kept in shared memory.  The rounding of the
+//    target position relative to the source tile centre, s = fl(o_i + dc), is
+//    the same for all sources of a unit and is undone to first order with
+//    the source tile's monopole tidal tensor (its exact value comes from
+//    Fast2Sum).  For the source side the per-target roundings are independent
+//    and average out.
+//  * Both sides are accumulated in 64-bit fixed point with red.global.add:
+//    every partial is scaled by a per-tile power of two, chosen from a bound
+//    on the tile's far-field sum computed by the classification pass, and
+//    rounded to an integer.  Integer addition is associative, so the result
+//    does not depend on the order of the atomic adds: evaluations are
+//    bit-for-bit reproducible.
+//  * Every mbarrier wait is bounded (%globaltimer); a wait that runs out
+//    records STEPS_ETIMEOUT, the producer drains its own copies and the CTA
+//    exits.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+
+#include "async_copy.cuh"
+#include "pair_terms.cuh"
+#include "steps_internal.h"
+#include "systems.cuh"
+
+namespace steps {
+
+namespace {
+
+constexpr int kKI = 8;                  // targets per lane
+constexpr int kKJ = 2;                  // sources per lane and step
+constexpr int kT = 32 * kKI;            // particles per tile
+constexpr int kR = kT / (32 * kKJ);     // rounds of 32 steps per source tile
+constexpr int kNP = kKI / 2;            // packed target pairs per lane
+constexpr int kFold = 16;               // steps (32 sources) per compensated fold
+
+struct SymArgs {
+    const float4 *__restrict__ sdup;      // [np / 32][2][32] (ox, ox, oy, oy), (oz, oz, m, m)
+    const float4 *__restrict__ tbox_c;    // [ntile] (cx, cy, cz, hmax)
+    const float4 *__restrict__ tbox_e;    // [ntile] (ex, ey, ez, tile mass)
+    const uint32_t *__restrict__ nearbits;
+    const float *__restrict__ tscale;     // [ntile] fixed-point scale
+    unsigned long long *__restrict__ acc; // [3][np]
+    int *nonfinite;
+    int *err;
+    const SimDesc *__restrict__ sims;
+    int nsims;
+    int64_t np;
+    int64_t units;
+    long long wait_ns;
+};
+
+// Units of one system in row-major order: row b holds (b, J) for
+// J = (b + 1) W .. ntile - 1.
+template <int W>
+struct UnitCursor {
+    int sidx;
+    SimDesc d;
+    int64_t b, J;
+
+    __device__ __forceinline__ int64_t row_off(int64_t bb) const {
+        return bb * d.ntile - (int64_t)W * bb * (bb + 1) / 2;
+    }
+    __device__ __forceinline__ void locate(const SimDesc *__restrict__ sims, int nsims, int64_t u) {
+        sidx = sim_of_unit(sims, nsims, u);
+        d = sims[sidx];
+        const int64_t v = u - d.unit_off;
+        int64_t lo = 0, hi = d.ntile / W - 1;  // row_off(lo) <= v < row_off(hi)
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (row_off(mid) <= v) lo = mid; else hi = mid;
+        }
+        b = lo;
+        J = (b + 1) * W + (v - row_off(b));
+    }
+    __device__ __forceinline__ void next(const SimDesc *__restrict__ sims, int nsims) {
+        if (++J < d.ntile) return;
+        ++b;
+        J = (b + 1) * W;
+        while (J >= d.ntile) {  // empty row: the next system with units
+            if (++sidx >= nsims) return;
+            d = sims[sidx];
+            b = 0;
+            J = W;
+        }
+    }
+};
+
+// Add v (FP32) times the power of two sc to a fixed-point sum.
+__device__ __forceinline__ void red_fixed(unsigned long long *addr, float v, float sc, int *nonfinite) {
+    if (!isfinite(v)) {
+        if (nonfinite) *nonfinite = 1;
+        return;
+    }
+    atomicAdd(addr, (unsigned long long)__float2ll_rn(v * sc));
+}
+
+// One far unit for this warp: the warp's 256 targets against the 256 sources
+// of the staged tile S.  meta = (dc, M_J).  Target sums go to the Kahan state
+// myk; source sums to the fixed-point array (scale scJ) of the source tile
+// starting at particle jbase.
+template <int UNR>
+__device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const float4 meta,
+                                             const float2 *__restrict__ myio, float4 *__restrict__ myk,
+                                             const float2 (&mi)[kNP], int lane, int64_t jbase, float scJ,
+                                             unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
+    const float2 neg1 = make_float2(-1.0f, -1.0f);
+    float2 nsx[kNP], nsy[kNP], nsz[kNP];  // -s, s = fl(o_i + dc): target relative to the source tile centre
+    float2 px[kNP], py[kNP], pz[kNP];     // FP32 target partials (the first starts at the shift correction)
+    {
+        const float2 dcx2 = make_float2(meta.x, meta.x), dcy2 = make_float2(meta.y, meta.y),
+                     dcz2 = make_float2(meta.z, meta.z);
+        const float2 ndx = make_float2(-meta.x, -meta.x), ndy = make_float2(-meta.y, -meta.y),
+                     ndz = make_float2(-meta.z, -meta.z);
+        const float2 M2 = make_float2(meta.w, meta.w);
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+            const float2 ox = myio[(0 * kNP + q) * 32 + lane];
+            const float2 oy = myio[(1 * kNP + q) * 32 + lane];
+            const float2 oz = myio[(2 * kNP + q) * 32 + lane];
+            nsx[q] = __ffma2_rn(ox, neg1, ndx);
+            nsy[q] = __ffma2_rn(oy, neg1, ndy);
+            nsz[q] = __ffma2_rn(oz, neg1, ndz);
+            // l = (o_i + dc) - s exactly (Fast2Sum: |dc| > |o_i| for every far pair)
+            const float2 lx = __fadd2_rn(ox, __fadd2_rn(nsx[q], dcx2));
+            const float2 ly = __fadd2_rn(oy, __fadd2_rn(nsy[q], dcy2));
+            const float2 lz = __fadd2_rn(oz, __fadd2_rn(nsz[q], dcz2));
+            // The true target sits at s + l: first-order change of the source
+            // tile's monopole field M (-x)/|x|^3 at x = s,
+            //   -M l/R^3 + 3 M s (s.l)/R^5,  R = |s|.
+            float2 R2 = __fmul2_rn(nsx[q], nsx[q]);
+            R2 = __ffma2_rn(nsy[q], nsy[q], R2);
+            R2 = __ffma2_rn(nsz[q], nsz[q], R2);
+            const float2 Ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
+            const float2 Ri2 = __fmul2_rn(Ri, Ri);
+            const float2 k1 = __fmul2_rn(__fmul2_rn(M2, Ri), Ri2);
+            float2 proj = __fmul2_rn(nsx[q], lx);
+            proj = __ffma2_rn(nsy[q], ly, proj);
+            proj = __ffma2_rn(nsz[q], lz, proj);
+            const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
+            const float2 nk1 = __fmul2_rn(k1, neg1);
+            px[q] = __ffma2_rn(k2, nsx[q], __fmul2_rn(nk1, lx));
+            py[q] = __ffma2_rn(k2, nsy[q], __fmul2_rn(nk1, ly));
+            pz[q] = __ffma2_rn(k2, nsz[q], __fmul2_rn(nk1, lz));
+        }
+    }
+    const int from = (lane + 1) & 31;
+#pragma unroll 1
+    for (int r = 0; r < kR; ++r) {
+        float2 Sx[kKJ], Sy[kKJ], Sz[kKJ];  // running sums of the sources of group (lane + step) mod 32
+#pragma unroll
+        for (int k = 0; k < kKJ; ++k) Sx[k] = Sy[k] = Sz[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int h = 0; h < 32; h += kFold) {
+#pragma unroll UNR
+            for (int st = h; st < h + kFold; ++st) {
+                const int g = (lane + st) & 31;
+#pragma unroll
+                for (int k = 0; k < kKJ; ++k) {
+                    const float4 *src = S + (r * kKJ + k) * 64 + g;
+                    const float4 A = src[0], B = src[32];
+                    const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+                    const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+#pragma unroll
+                    for (int q = 0; q < kNP; ++q) {
+                        const float2 dx = __fadd2_rn(xj, nsx[q]);  // x_j - x_i
+                        const float2 dy = __fadd2_rn(yj, nsy[q]);
+                        const float2 dz = __fadd2_rn(zj, nsz[q]);
+                        float2 r2 = __fmul2_rn(dx, dx);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dz, dz, r2);
+                        const float2 w = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                        const float2 u = __fmul2_rn(__fmul2_rn(w, w), w);  // 1/r^3
+                        const float2 si = __fmul2_rn(u, mj);
+                        px[q] = __ffma2_rn(si, dx, px[q]);
+                        py[q] = __ffma2_rn(si, dy, py[q]);
+                        pz[q] = __ffma2_rn(si, dz, pz[q]);
+                        const float2 sj = __fmul2_rn(u, mi[q]);
+                        Sx[k] = __ffma2_rn(sj, dx, Sx[k]);
+                        Sy[k] = __ffma2_rn(sj, dy, Sy[k]);
+                        Sz[k] = __ffma2_rn(sj, dz, Sz[k]);
+                    }
+                }
+                // pass the group's sums on: lane l takes over group (l + st + 1) mod 32
+#pragma unroll
+                for (int k = 0; k < kKJ; ++k) {
+                    Sx[k].x = __shfl_sync(0xffffffffu, Sx[k].x, from);
+                    Sx[k].y = __shfl_sync(0xffffffffu, Sx[k].y, from);
+                    Sy[k].x = __shfl_sync(0xffffffffu, Sy[k].x, from);
+                    Sy[k].y = __shfl_sync(0xffffffffu, Sy[k].y, from);
+                    Sz[k].x = __shfl_sync(0xffffffffu, Sz[k].x, from);
+                    Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
+                }
+            }
+            // fold the target partials into the compensated sums
+#pragma unroll
+            for (int q = 0; q < kNP; ++q) {
+                float4 *K = myk + q * 32 + lane;
+                float4 kx = K[0], ky = K[kNP * 32], kz = K[2 * kNP * 32];
+                float2 hx = make_float2(kx.x, kx.y), cx = make_float2(kx.z, kx.w);
+                float2 hy = make_float2(ky.x, ky.y), cy = make_float2(ky.z, ky.w);
+                float2 hz = make_float2(kz.x, kz.y), cz = make_float2(kz.z, kz.w);
+                kahan2(hx, cx, px[q]);
+                kahan2(hy, cy, py[q]);
+                kahan2(hz, cz, pz[q]);
+                K[0] = make_float4(hx.x, hx.y, cx.x, cx.y);
+                K[kNP * 32] = make_float4(hy.x, hy.y, cy.x, cy.y);
+                K[2 * kNP * 32] = make_float4(hz.x, hz.y, cz.x, cz.y);
+                px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+            }
+        }
+        // this lane now holds its own group: sources (r, k, lane); the force on
+        // a source is minus the sum of m_i (x_j - x_i) / r^3
+#pragma unroll
+        for (int k = 0; k < kKJ; ++k) {
+            const int64_t idx = jbase + (r * kKJ + k) * 32 + lane;
+            red_fixed(acc + idx, -(Sx[k].x + Sx[k].y), scJ, nonfinite);
+            red_fixed(acc + np + idx, -(Sy[k].x + Sy[k].y), scJ, nonfinite);
+            red_fixed(acc + 2 * np + idx, -(Sz[k].x + Sz[k].y), scJ, nonfinite);
+        }
+    }
+}
+
+template <int W, int NS, int MINB, int UNR>
+__global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymArgs a) {
+    constexpr uint32_t BYTES_J = kT * 32u;
+    extern __shared__ __align__(128) unsigned char smem[];
+    float4 *sj = reinterpret_cast<float4 *>(smem);                         // [NS][2 kT] source tiles
+    float4 *smeta = sj + NS * 2 * kT;                                      // [NS][W] (dc, M_J or -1: near)
+    float2 *sio = reinterpret_cast<float2 *>(smeta + NS * W);              // [W][3][kNP][32] target offsets
+    float4 *skah = reinterpret_cast<float4 *>(sio + W * 3 * kNP * 32);     // [W][3][kNP][32] Kahan (hi, -c)
+    uint64_t *bars = reinterpret_cast<uint64_t *>(skah + W * 3 * kNP * 32);  // full[NS], empty[NS]
+
+    const int warp = threadIdx.x >> 5;
+    const int lane = threadIdx.x & 31;
+    const int64_t G = gridDim.x;
+    const int64_t cta = blockIdx.x;
+    const int64_t u0 = cta * a.units / G;
+    const int64_t u1 = (cta + 1) * a.units / G;
+    const int64_t count = u1 - u0;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < NS; ++s) {
+            mbar_init(smem_u32(&bars[s]), 1);
+            mbar_init(smem_u32(&bars[NS + s]), W);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (count <= 0) return;
+
+    if (warp == W) {
+        // ---------------- producer warp ----------------
+        UnitCursor<W> c;
+        c.locate(a.sims, a.nsims, u0);
+        int64_t k = 0;
+        bool ok = true;
+        for (; k < count; ++k) {
+            const int s = (int)(k % NS);
+            if (k >= NS) {
+                bool got = true;
+                if (lane == 0)
+                    got = mbar_wait_bounded(smem_u32(&bars[NS + s]), (uint32_t)(((k / NS) - 1) & 1), a.wait_ns);
+                if (!__shfl_sync(0xffffffffu, got, 0)) {
+                    ok = false;
+                    break;
+                }
+            }
+            const int64_t jg = c.d.tile_off + c.J;
+            if (lane < W) {
+                const int64_t il = c.b * W + lane;
+                const uint32_t word = a.nearbits[c.d.bits_off + il * c.d.words + (c.J >> 5)];
+                const bool near = (word >> (c.J & 31)) & 1u;
+                const float4 ci = a.tbox_c[c.d.tile_off + il], cj = a.tbox_c[jg];
+                // exact: the tile centres lie on a common grid (staging)
+                smeta[s * W + lane] = make_float4(__fsub_rn(ci.x, cj.x), __fsub_rn(ci.y, cj.y),
+                                                  __fsub_rn(ci.z, cj.z), near ? -1.f : a.tbox_e[jg].w);
+            }
+            __syncwarp();
+            if (lane == 0) {
+                __threadfence_block();  // the other lanes' metadata before the release-arrive
+                const uint32_t full = smem_u32(&bars[s]);
+                mbar_arrive_expect_tx(full, BYTES_J);
+                bulk_g2s(smem_u32(sj + (size_t)s * 2 * kT), a.sdup + jg * 2 * kT, BYTES_J, full);
+            }
+            c.next(a.sims, a.nsims);
+        }
+        if (lane == 0) {
+            if (!ok) atomicExch(a.err, (int)STEPS_ETIMEOUT);
+            // drain: every copy this warp issued must land before the CTA may exit
+            const int64_t first = k > NS ? k - NS : 0;
+            for (int64_t q = first; q < k; ++q)
+                if (!mbar_wait_bounded(smem_u32(&bars[q % NS]), (uint32_t)((q / NS) & 1), kDrainNs))
+                    atomicExch(a.err, (int)STEPS_ETIMEOUT);
+        }
+        return;
+    }
+
+    // ---------------- compute warps ----------------
+    float2 *myio = sio + warp * 3 * kNP * 32;
+    float4 *myk = skah + warp * 3 * kNP * 32;
+    UnitCursor<W> c;
+    c.locate(a.sims, a.nsims, u0);
+    int64_t u = u0;
+    int64_t k = 0;
+    while (u < u1) {
+        const int64_t seg_end = min(u1, c.d.unit_off + c.row_off(c.b + 1));
+        const int64_t ig = c.d.tile_off + c.b * W + warp;  // this warp's target tile
+        float2 mi[kNP];
+        __syncwarp();
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+            const float4 *p0 = a.sdup + (ig * kKI + 2 * q) * 64 + lane;  // particle 64 q + lane
+            const float4 *p1 = p0 + 64;                                   // particle 64 q + 32 + lane
+            const float4 A0 = p0[0], B0 = p0[32], A1 = p1[0], B1 = p1[32];
+            myio[(0 * kNP + q) * 32 + lane] = make_float2(A0.x, A1.x);
+            myio[(1 * kNP + q) * 32 + lane] = make_float2(A0.z, A1.z);
+            myio[(2 * kNP + q) * 32 + lane] = make_float2(B0.x, B1.x);
+            mi[q] = make_float2(B0.z, B1.z);
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) myk[(cc * kNP + q) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        __syncwarp();
+        for (; u < seg_end; ++u, ++k) {
+            const int s = (int)(k % NS);
+            if (!mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((k / NS) & 1), a.wait_ns)) {
+                if (lane == 0) atomicExch(a.err, (int)STEPS_ETIMEOUT);
+                return;
+            }
+            const float4 meta = smeta[s * W + warp];
+            if (meta.w >= 0.f) {
+                const int64_t jg = c.d.tile_off + c.J;
+                sym_far_unit<UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT, a.tscale[jg],
+                                  a.acc, a.np, a.nonfinite);
+            }
+            // release the stage so the producer can refill it
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(&bars[NS + s]));
+            c.next(a.sims, a.nsims);
+        }
+        // ---- segment done: this warp's target sums into the fixed-point array ----
+        const float scI = a.tscale[ig];
+#pragma unroll
+        for (int q = 0; q < kNP; ++q) {
+#pragma unroll
+            for (int cc = 0; cc < 3; ++cc) {
+                const float4 K = myk[(cc * kNP + q) * 32 + lane];
+                unsigned long long *dst = a.acc + cc * a.np + ig * kT + 64 * q + lane;
+                red_fixed(dst, K.x, scI, a.nonfinite);
+                red_fixed(dst, K.z, scI, a.nonfinite);
+                red_fixed(dst + 32, K.y, scI, a.nonfinite);
+                red_fixed(dst + 32, K.w, scI, a.nonfinite);
+            }
+        }
+    }
+}
+
+// Near bitmap of every ordered tile pair of a system (pairs inside one target
+// block are near: the far kernel's units start after the block), and the
+// per-tile fixed-point scale.  The scale bounds the tile's far-field sums: a
+// far pair of tiles contributes at most M_J / gap^2 to any particle of I (gap
+// = the distance between their boxes, r >= gap for every pair), so every
+// partial sum of tile I stays below B_I = sum_J M_J / gap_IJ^2; with
+// 2 B_I < 2^E the scale 2^(62 - E) keeps every fixed-point value below 2^61.
+// One warp per tile row.
+template <int W>
+__global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const float4 *__restrict__ tbox_e,
+                                    const SimDesc *__restrict__ sims, int nsims, int64_t ntile_all,
+                                    float alpha2, uint32_t *__restrict__ bits, float *__restrict__ tscale,
+                                    double *__restrict__ tinv, unsigned long long *stats) {
+    const int64_t row = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (row >= ntile_all) return;
+    const SimDesc d = sims[sim_of_tile(sims, nsims, row)];
+    const int64_t I = row - d.tile_off;
+    const float4 ci = tbox_c[row], ei = tbox_e[row];
+    double bound = 0.0;
+    unsigned long long nn = 0;
+    for (int64_t j0 = 0; j0 < d.ntile; j0 += 32) {
+        const int64_t J = j0 + lane;
+        bool near = false;
+        if (J < d.ntile) {
+            if (J / W == I / W) {
+                near = true;
+            } else {
+                const float4 cj = tbox_c[d.tile_off + J], ej = tbox_e[d.tile_off + J];
+                float gap2 = 0.f;
+                near = tile_pair_near(ci, ei, cj, ej, alpha2, &gap2);
+                if (!near) bound += (double)ej.w / (double)gap2;
+            }
+        }
+        const unsigned word = __ballot_sync(0xffffffffu, near);
+        if (lane == 0) bits[d.bits_off + I * d.words + (j0 >> 5)] = word;
+        nn += near ? 1 : 0;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        bound += __shfl_xor_sync(0xffffffffu, bound, o);
+        nn += __shfl_xor_sync(0xffffffffu, nn, o);
+    }
+    if (lane == 0) {
+        int e = -200;
+        if (bound > 0.0) frexp(2.0 * bound, &e);  // 2 B < 2^e
+        int sh = 62 - e;
+        sh = sh > 126 ? 126 : (sh < -126 ? -126 : sh);
+        tscale[row] = ldexpf(1.0f, sh);
+        tinv[row] = ldexp(1.0, -sh);
+        if (stats) {
+            atomicAdd(&stats[0], nn);
+            atomicAdd(&stats[1], (unsigned long long)d.ntile);
+        }
+    }
+}
+
+// acc = G (far field in fixed point + near-field items in item order), sorted order.
+__global__ void sym_fixup_kernel(const unsigned long long *__restrict__ acc, int64_t np,
+                                 const double *__restrict__ tinv, const double *__restrict__ item_part,
+                                 const int64_t *__restrict__ item_off, int64_t n, double Gc,
+                                 double *__restrict__ ax, double *__restrict__ ay, double *__restrict__ az,
+                                 int *nonfinite) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int64_t row = p / kT;
+    const int li = (int)(p - row * kT);
+    double sx = 0.0, sy = 0.0, sz = 0.0;
+    for (int64_t it = item_off[row]; it < item_off[row + 1]; ++it) {
+        const double *Q = item_part + (size_t)it * 3 * kT;
+        sx += Q[li];
+        sy += Q[kT + li];
+        sz += Q[2 * kT + li];
+    }
+    const double inv = tinv[row];
+    sx += (double)(long long)acc[p] * inv;
+    sy += (double)(long long)acc[np + p] * inv;
+    sz += (double)(long long)acc[2 * np + p] * inv;
+    ax[p] = Gc * sx;
+    ay[p] = Gc * sy;
+    az[p] = Gc * sz;
+    if (nonfinite && (!isfinite(sx) || !isfinite(sy) || !isfinite(sz))) *nonfinite = 1;
+}
+
+constexpr int kNS = 2;
+constexpr int kUNR = 2;
+
+template <int W>
+constexpr size_t sym_smem_of() {
+    return (size_t)kNS * 2 * kT * 16 + (size_t)kNS * W * 16 + (size_t)W * 3 * kNP * 32 * 8 +
+           (size_t)W * 3 * kNP * 32 * 16 + 2 * kNS * sizeof(uint64_t);
+}
+
+using SymFn = void (*)(const SymArgs);
+
+SymFn sym_fn(int W) {
+    switch (W) {
+        case 4: return sym_far_kernel<4, kNS, 3, kUNR>;
+        default: return nullptr;
+    }
+}
+
+}  // namespace
+
+int64_t sym_units(int64_t ntile, int W) {
+    const int64_t nb = ntile / W;
+    return nb >= 1 ? (nb - 1) * ntile - (int64_t)W * (nb - 1) * nb / 2 : 0;
+}
+
+size_t sym_smem_bytes(int W, int NS) {
+    (void)NS;
+    return W == 4 ? sym_smem_of<4>() : 0;
+}
+
+int sym_blocks_per_sm(int W, int NS) {
+    SymFn fn = sym_fn(W);
+    if (!fn) return 0;
+    const size_t smem = sym_smem_bytes(W, NS);
+    cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    int per = 1;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, (W + 1) * 32, smem) != cudaSuccess || per < 1)
+        per = 1;
+    return per;
+}
+
+cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const NearScratch &nr, float alpha,
+                                unsigned long long *stats, cudaStream_t st) {
+    const int W = variant(p.variant).W;
+    const unsigned blocks = (unsigned)((s.ntile * 32 + 255) / 256);
+    if (W != 4) return cudaErrorInvalidValue;
+    sym_classify_kernel<4><<<blocks, 256, 0, st>>>(s.tbox_c, s.tbox_e, p.sims, p.nsims, s.ntile, alpha * alpha,
+                                                   nr.bits, nr.tscale, nr.tinv, stats);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScratch &nr, int *err,
+                           long long wait_ns, cudaStream_t st) {
+    const int W = variant(p.variant).W;
+    SymFn fn = sym_fn(W);
+    if (!fn) return cudaErrorInvalidValue;
+    SymArgs a;
+    a.sdup = s.sdup;
+    a.tbox_c = s.tbox_c;
+    a.tbox_e = s.tbox_e;
+    a.nearbits = nr.bits;
+    a.tscale = nr.tscale;
+    a.acc = nr.sym_acc;
+    a.nonfinite = nr.nonfinite;
+    a.err = err;
+    a.sims = p.sims;
+    a.nsims = p.nsims;
+    a.np = s.np;
+    a.units = p.units;
+    a.wait_ns = wait_ns;
+    if (p.units <= 0) return cudaSuccess;
+    fn<<<p.grid, (W + 1) * 32, sym_smem_bytes(W, kNS), st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_sym_fixup(const Staging &s, const ForcePlan &p, const NearScratch &nr, double G,
+                             double *ax, double *ay, double *az, cudaStream_t st) {
+    (void)p;
+    const int tb = 256;
+    const int64_t blocks = (s.n + tb - 1) / tb;
+    sym_fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(nr.sym_acc, s.np, nr.tinv, nr.item_part, nr.item_off, s.n,
+                                                      G, ax, ay, az, nr.nonfinite);
+    return cudaGetLastError();
+}
+
+}  // namespace steps

@@ -184,4 +184,37 @@ __device__ __forceinline__ void near_tile_terms(
     }
 }
 
+// Tile-pair classification (done once per pair by the far-field producer;
+// the near-field kernel reads the resulting bitmap).  Conservative margins of
+// 2^-18 cover the FP32 rounding of the box arithmetic.
+//  * near if some pair may be closer than h_i + h_j (spline branches of Eq. 4);
+//  * near if the boxes are closer than alpha x (|c_I - c_J| + |e_I| + |e_J|),
+//    where one FP32 difference of offsets could lose relative precision in d;
+//  * near if |e_I| + |e_J| > |c_I - c_J|: the far field's first-order
+//    correction of the target shift uses the source tile's monopole tidal
+//    tensor, which needs the tiles to be smaller than their distance.
+// gap2_out (may be null) receives the squared distance between the two boxes
+// (rounded down), which bounds r^2 from below for every pair of the tiles.
+__device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei, const float4 cj,
+                                               const float4 ej, const float alpha2,
+                                               float *gap2_out = nullptr) {
+    const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
+    const float dcx = __fsub_rn(ci.x, cj.x), dcy = __fsub_rn(ci.y, cj.y), dcz = __fsub_rn(ci.z, cj.z);
+    const float gx = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcx), dn), __fmul_rn(__fadd_rn(ei.x, ej.x), up)));
+    const float gy = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcy), dn), __fmul_rn(__fadd_rn(ei.y, ej.y), up)));
+    const float gz = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcz), dn), __fmul_rn(__fadd_rn(ei.z, ej.z), up)));
+    const float gap2 = __fadd_rn(__fadd_rn(__fmul_rn(gx, gx), __fmul_rn(gy, gy)), __fmul_rn(gz, gz));
+    if (gap2_out) *gap2_out = gap2;
+    const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
+    if (gap2 <= __fmul_rn(hs, hs)) return true;
+    const float n2 = __fadd_rn(__fadd_rn(__fmul_rn(dcx, dcx), __fmul_rn(dcy, dcy)), __fmul_rn(dcz, dcz));
+    const float ni = __fadd_rn(__fadd_rn(__fmul_rn(ei.x, ei.x), __fmul_rn(ei.y, ei.y)), __fmul_rn(ei.z, ei.z));
+    const float nj = __fadd_rn(__fadd_rn(__fmul_rn(ej.x, ej.x), __fmul_rn(ej.y, ej.y)), __fmul_rn(ej.z, ej.z));
+    const float dist = __fsqrt_rn(n2);
+    const float ext = __fadd_rn(__fsqrt_rn(ni), __fsqrt_rn(nj));
+    if (__fmul_rn(ext, up) > dist) return true;
+    const float scale = __fadd_rn(dist, ext);
+    return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
+}
+
 }  // namespace steps

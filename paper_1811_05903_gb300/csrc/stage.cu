@@ -42,11 +42,31 @@ struct SumOp {
 };
 
 // One CTA per tile, blockDim.x == T.
+// Largest |coordinate| of the real particles into *out (the bit pattern of a
+// non-negative double orders like the value, so an integer max is exact).
+__global__ void absmax_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                              const double *__restrict__ z, const double *__restrict__ h,
+                              unsigned long long *__restrict__ out) {
+    double v = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        if (!(h[i] < 0.0)) v = fmax(v, fmax(fabs(x[i]), fmax(fabs(y[i]), fabs(z[i]))));
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
+}
+
+// Tile centre component rounded to the grid q (q = 0: no rounding).  With
+// max|x| < 2^e and q = 2^(e-22), a rounded centre has at most 23 significant
+// bits and the difference of two centres at most 24: both exact in FP32.
+__device__ __forceinline__ float grid_centre(double mid, double q) {
+    return q > 0.0 ? (float)(rint(mid / q) * q) : __double2float_rn(mid);
+}
+
 __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              const double *__restrict__ y, const double *__restrict__ z,
                              const double *__restrict__ m, const double *__restrict__ h,
                              float4 *__restrict__ jdup, float4 *__restrict__ rdup,
-                             float4 *__restrict__ fdup, float4 *__restrict__ tbox_c,
+                             float4 *__restrict__ fdup, float4 *__restrict__ sdup,
+                             const unsigned long long *__restrict__ qmax, float4 *__restrict__ tbox_c,
                              float4 *__restrict__ tbox_e) {
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
@@ -70,9 +90,18 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     const double mass = block_reduce(valid ? pm : 0.0, sbuf, SumOp());
     const bool any = lox <= hix;  // tile holds at least one real particle
     // FP32 centre (exactly representable), FP64 offsets rounded once to FP32
-    const float cx = any ? __double2float_rn(0.5 * (lox + hix)) : 0.f;
-    const float cy = any ? __double2float_rn(0.5 * (loy + hiy)) : 0.f;
-    const float cz = any ? __double2float_rn(0.5 * (loz + hiz)) : 0.f;
+    double q = 0.0;
+    if (qmax) {
+        const double amax = __longlong_as_double((long long)*qmax);
+        int e = 0;
+        if (amax > 0.0) {
+            frexp(amax, &e);  // amax < 2^e
+            q = ldexp(1.0, e - 22);
+        }
+    }
+    const float cx = any ? grid_centre(0.5 * (lox + hix), q) : 0.f;
+    const float cy = any ? grid_centre(0.5 * (loy + hiy), q) : 0.f;
+    const float cz = any ? grid_centre(0.5 * (loz + hiz), q) : 0.f;
     const double dx = px - (double)cx, dy = py - (double)cy, dz = pz - (double)cz;
     const double ex = block_reduce(valid ? fabs(dx) : 0.0, sbuf, MaxOp());
     const double ey = block_reduce(valid ? fabs(dy) : 0.0, sbuf, MaxOp());
@@ -97,6 +126,12 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     jdup[2 * p + 1] = make_float4(oz, oz, fm, fm);
     rdup[2 * p] = make_float4(rx, rx, ry, ry);
     rdup[2 * p + 1] = make_float4(rz, rz, fh, fh);
+    if (sdup) {
+        // chunks of 32 particles, component-major inside a chunk
+        const int64_t base = (p >> 5) * 64 + (p & 31);
+        sdup[base] = make_float4(ox, ox, oy, oy);
+        sdup[base + 32] = make_float4(oz, oz, fm, fm);
+    }
     if (fdup) {
         // Far-field expansion: with k = m^(-2/3) rounded once to FP32,
         //   k |o_j - s|^2 = k |s|^2 + k |o_j|^2 - 2 k o_j . s
@@ -263,8 +298,12 @@ inline unsigned blocks_for(int64_t n, int tb) { return (unsigned)((n + tb - 1) /
 
 void launch_stage(const Staging &s, const double *x, const double *y, const double *z,
                   const double *m, const double *h, cudaStream_t st) {
+    if (s.qmax) {
+        cudaMemsetAsync(s.qmax, 0, sizeof(unsigned long long), st);
+        absmax_kernel<<<152, 512, 0, st>>>(s.n, x, y, z, h, s.qmax);
+    }
     stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup,
-                                                    s.fdup, s.tbox_c, s.tbox_e);
+                                                    s.fdup, s.sdup, s.qmax, s.tbox_c, s.tbox_e);
 }
 
 namespace {

@@ -44,7 +44,10 @@ struct Variant {
     // far-field arithmetic: 0 = explicit separation d = o_j - s (12 FP32 lane
     // operations per interaction), 1 = expansion of |o_j - s|^2 about the
     // source tile centre with the mass folded into the squared distance
-    // (10 lane operations; reads Staging::fdup)
+    // (10 lane operations; reads Staging::fdup), 2 = symmetric: every far pair
+    // of tiles (I < J) is evaluated once and its force is added to both
+    // particles (explicit separation, 8 lane operations and half an MUFU per
+    // interaction; reads Staging::sdup, accumulates in fixed point)
     int form;
 };
 
@@ -63,6 +66,14 @@ struct Staging {
     // (ox, ox, oy, oy), (oz, oz, k, k), (2k ox, 2k ox, 2k oy, 2k oy), (2k oz, 2k oz, k |o|^2, k |o|^2)
     // with k = fl(m^(-2/3)); padding: o = 1e15, k = 1e10, 2k o = 0, k |o|^2 = +inf
     float4 *fdup = nullptr;
+    // [2 np] symmetric-kernel layout, or null: per 32-particle chunk of a tile,
+    // 32 x (ox, ox, oy, oy) then 32 x (oz, oz, m, m); padding: o = 1e15, m = 0
+    float4 *sdup = nullptr;
+    // device word for the largest |coordinate| (bit pattern of a non-negative
+    // double), or null.  When set, tile centres are rounded to multiples of
+    // 2^(e-22) with max|x| < 2^e, so that every difference of two centres is
+    // exact in FP32.
+    unsigned long long *qmax = nullptr;
     float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
 };
@@ -93,6 +104,11 @@ struct NearScratch {
     double *item_part = nullptr;  // [cap_items][3][T]
     int64_t cap_items = 0;
     int64_t bits_words = 0;       // words of `bits` in use (cleared per evaluation)
+    // symmetric kernel (Variant::form == 2) only:
+    unsigned long long *sym_acc = nullptr;  // [3][np] fixed-point far-field sums
+    float *tscale = nullptr;                // [ntile] 2^(62 - E_t): FP32 value -> fixed point
+    double *tinv = nullptr;                 // [ntile] 2^(E_t - 62)
+    int *nonfinite = nullptr;               // set to 1 when a far-field partial is not finite
 };
 
 // Stream-K plan for one FP32 force evaluation over one or more systems.
@@ -109,6 +125,22 @@ struct ForcePlan {
 };
 
 ForcePlan plan_force(const Staging &s, int variant, int num_sms);
+
+// Symmetric far field (force_sym.cu).  Units are (target block b of W tiles,
+// source tile J) with J >= (b + 1) W, per system; pairs of tiles inside one
+// block go to the near field.
+int64_t sym_units(int64_t ntile, int W);
+size_t sym_smem_bytes(int W, int NS);
+int sym_blocks_per_sm(int W, int NS);
+// Near bitmap (all ordered tile pairs; same-block pairs are near), per-tile
+// fixed-point scales from a bound on the far-field sums, near/all counts.
+cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const NearScratch &nr, float alpha,
+                                unsigned long long *stats, cudaStream_t st);
+cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScratch &nr, int *err,
+                           long long wait_ns, cudaStream_t st);
+// acc = G (fixed-point far field + near-field items), sorted order.
+cudaError_t launch_sym_fixup(const Staging &s, const ForcePlan &p, const NearScratch &nr, double G,
+                             double *ax, double *ay, double *az, cudaStream_t st);
 // Plan for several systems: descs is the host copy of the table (its unit_off,
 // blk_off and bits_off are filled in here); dev_sims the device copy to use.
 ForcePlan plan_force_multi(int variant, int num_sms, SimDesc *descs, int nsims,
@@ -251,6 +283,9 @@ cudaError_t launch_softening(int64_t n, const double *m, double h_min, double *h
 // Input check: *flag |= 1 if a holds NaN/Inf, |= 2 if positive != 0 and some a[i] <= 0.
 cudaError_t launch_check_finite(int64_t n, const double *a, int positive, int *flag,
                                 cudaStream_t st);
+// *flag = 1 if some a[i], b[i] or c[i], i < n, is NaN or Inf (the non-finite result check).
+cudaError_t launch_check_finite3(int64_t n, const double *a, const double *b, const double *c, int *flag,
+                                 cudaStream_t st);
 cudaError_t launch_set_scalar(double *sc, int slot, double v, cudaStream_t st);
 
 }  // namespace steps

@@ -145,3 +145,59 @@ def test_precision_study_full_size_sampled():
     net = np.abs((p.mass[:, None] * a).sum(0))
     scale = (p.mass[:, None] * np.abs(a)).sum()
     assert np.all(net <= 1e-6 * scale)
+
+
+def sym_variant():
+    """1-based index of the symmetric far-field variant (tile_override)."""
+    names = steps.steps_variants()
+    return names.index("sym_ki8_w4") + 1
+
+
+@pytest.mark.parametrize("n", [1, 2, 255, 256, 257, 1023, 1024, 1025, 4096 + 77, 9000])
+def test_symmetric_small_and_ragged_sizes(n):
+    """The symmetric far field (each far pair once, applied to both particles):
+    sizes from below one tile to several blocks with a ragged last tile."""
+    rng = np.random.default_rng(100 + n)
+    pos = rng.normal(size=(n, 3)) * np.array([1.0, 2.0, 0.5])
+    m = rng.uniform(0.5, 2.0, n)
+    h = rng.uniform(0.001, 0.05, n)
+    p = workloads.Particles(pos=pos, vel=np.zeros_like(pos), mass=m, h_min=0.0)
+    a = gpu_forces(p, steps.STEPS_F32_COMP, h=h, tile_override=sym_variant())
+    if n == 1:
+        assert np.all(a == 0.0)
+        return
+    ref = oracle.pair_acc(pos, m, h, 1.0)
+    e = rel_err(a, ref)
+    assert np.sqrt(np.mean(e ** 2)) <= RMS_TOL and e.max() <= MAX_TOL, (n, np.sqrt(np.mean(e ** 2)), e.max())
+
+
+@pytest.mark.parametrize("n_central,per_shell", [(16384, 256), (16384 + 301, 128 + 5)])
+def test_symmetric_compactified_and_third_law(n_central, per_shell):
+    """Compactified set (mass ratio ~1e6 between shells and centre): parity with
+    the oracle, and the symmetric construction conserves momentum: the far
+    field adds +f to one particle and -f to the other in fixed point."""
+    p = workloads.compactified(22, n_central, 64, per_shell)
+    h = oracle.softening(p.mass, p.h_min)
+    ref = oracle.pair_acc(p.pos, p.mass, h, p.G)
+    a = gpu_forces(p, steps.STEPS_F32_COMP, tile_override=sym_variant(), comoving=True)
+    e = rel_err(a, ref)
+    rms = np.sqrt(np.mean(e ** 2))
+    assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
+    net = np.abs((p.mass[:, None] * a).sum(0))
+    scale = (p.mass[:, None] * np.abs(a)).sum()
+    assert np.all(net <= 1e-6 * scale), net / scale
+
+
+def test_symmetric_bitwise_reproducible():
+    """Fixed-point accumulation: the order of the atomic adds does not matter,
+    so two evaluations of the same state are bit-for-bit equal."""
+    p = workloads.compactified(23, 8192, 32, 128)
+    cfg = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_COMP, G=p.G, Om=p.Om, OL=p.OL,
+                            tile_override=sym_variant())
+    sim = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg)
+    try:
+        a1 = sim.forces()
+        a2 = sim.forces()
+    finally:
+        sim.close()
+    assert np.array_equal(a1, a2)
