@@ -44,16 +44,31 @@ __device__ __forceinline__ unsigned long long global_ns() {
     return t;
 }
 
+// As mbar_try_wait, but a thread whose phase is not yet complete is suspended
+// for up to about hint_ns nanoseconds (it issues nothing meanwhile) before
+// the call returns false.
+__device__ __forceinline__ bool mbar_try_wait_suspend(uint32_t bar, uint32_t parity, uint32_t hint_ns) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok)
+        : "r"(bar), "r"(parity), "r"(hint_ns)
+        : "memory");
+    return ok != 0;
+}
+
 // Wait for phase `parity` of an mbarrier to complete, giving up after
 // limit_ns nanoseconds (limit_ns == 0: give up at once; used by tests).
+// Waiting threads are suspended between checks rather than spinning, so a
+// warp that waits for a stage takes no issue slots from the warps that compute.
 __device__ __forceinline__ bool mbar_wait_bounded(uint32_t bar, uint32_t parity, long long limit_ns) {
     if (limit_ns == 0) return false;
     if (mbar_try_wait(bar, parity)) return true;
     const unsigned long long t0 = global_ns();
     for (;;) {
-#pragma unroll 1
-        for (int i = 0; i < 16; ++i)
-            if (mbar_try_wait(bar, parity)) return true;
+        if (mbar_try_wait_suspend(bar, parity, 20000u)) return true;
         if ((long long)(global_ns() - t0) > limit_ns) return false;
     }
 }

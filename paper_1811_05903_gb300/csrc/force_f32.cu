@@ -596,10 +596,11 @@ __global__ void near_count_kernel(const uint32_t *__restrict__ bits, const SimDe
     if (lane == 0) cnt[row] = c;
 }
 
-// Work items: row r contributes ceil(cnt[r] / chunk) items; item_off is the
+// Work items: row r contributes halves x ceil(cnt[r] / chunk) items (halves:
+// the parts of the target tile one warp takes at a time); item_off is the
 // exclusive scan.  chunk starts at kNearChunk and grows if the item buffer
 // (cap items) would overflow.  meta = {chunk, items, work counter}.  One CTA.
-__global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int64_t cap,
+__global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int64_t cap, int halves,
                                  int64_t *__restrict__ item_off, int64_t *__restrict__ meta) {
     __shared__ int64_t part[1024];
     __shared__ int64_t s_chunk;
@@ -614,13 +615,13 @@ __global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int
         int64_t all = 0;
         for (int k = 0; k < (int)blockDim.x; ++k) all += part[k];
         int64_t chunk = kNearChunk;
-        while (ntile + (all + chunk - 1) / chunk > cap) chunk *= 2;
+        while (halves * (ntile + (all + chunk - 1) / chunk) > cap) chunk *= 2;
         s_chunk = chunk;
     }
     __syncthreads();
     const int64_t chunk = s_chunk;
     int64_t items = 0;
-    for (int64_t r = r0; r < r1; ++r) items += (cnt[r] + chunk - 1) / chunk;
+    for (int64_t r = r0; r < r1; ++r) items += halves * ((cnt[r] + chunk - 1) / chunk);
     __syncthreads();
     part[t] = items;
     __syncthreads();
@@ -640,7 +641,7 @@ __global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int
     int64_t run = part[t];
     for (int64_t r = r0; r < r1; ++r) {
         item_off[r] = run;
-        run += (cnt[r] + chunk - 1) / chunk;
+        run += halves * ((cnt[r] + chunk - 1) / chunk);
     }
 }
 
@@ -655,17 +656,31 @@ __global__ void near_scan_kernel(const int *__restrict__ cnt, int64_t ntile, int
 // are summed in packed FP32x2 on the Newtonian branch; where some lane of the
 // warp meets a pair inside h_i + h_j the full spline of Eq. 4 is taken for
 // that source.  Self pairs (d == 0 exactly) contribute nothing.
+// NB source buffers per warp: 2 (the next tile's copy overlaps this tile's
+// terms) up to 128-particle tiles; 256-particle tiles take 1 so that three
+// CTAs fit on an SM (other warps cover the copy latency).
+template <int KI>
+constexpr int near_buffers() { return KI >= 8 ? 1 : 2; }
+// Targets per lane in one work item: a 256-particle tile is taken in two
+// halves of 128 targets (separate items), which keeps the register footprint
+// of the 128-particle kernel.
+template <int KI>
+constexpr int near_ti() { return KI == 8 ? 4 : KI; }
+
 template <int KI, bool COMP, int FOLD>
 __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceArgs a) {
     constexpr int T = 32 * KI;
-    constexpr int NPAIR = KI / 2;
+    constexpr int TI = near_ti<KI>();
+    constexpr int H = KI / TI;      // items per (row, chunk)
+    constexpr int NPAIR = TI / 2;
+    constexpr int NB = near_buffers<KI>();
     constexpr uint32_t BYTES = T * 64u;  // jdup + rdup of one tile
     extern __shared__ __align__(128) unsigned char smem[];
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    float4 *buf = reinterpret_cast<float4 *>(smem) + (size_t)warp * 2 * 4 * T;  // [2][jdup 2T | rdup 2T]
+    float4 *buf = reinterpret_cast<float4 *>(smem) + (size_t)warp * NB * 4 * T;  // [NB][jdup 2T | rdup 2T]
     uint64_t *bars =
-        reinterpret_cast<uint64_t *>(reinterpret_cast<float4 *>(smem) + kNearWarps * 8 * T) + 2 * warp;
+        reinterpret_cast<uint64_t *>(reinterpret_cast<float4 *>(smem) + kNearWarps * NB * 4 * T) + 2 * warp;
     if (lane == 0) {
         mbar_init(smem_u32(&bars[0]), 1);
         mbar_init(smem_u32(&bars[1]), 1);
@@ -698,14 +713,15 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
             if (a.item_off[mid] <= item) lo = mid; else hi_r = mid;
         }
         const int64_t itile = lo;
-        const int64_t first = (item - a.item_off[itile]) * chunk;
+        const int half = (int)((item - a.item_off[itile]) % H);
+        const int64_t first = ((item - a.item_off[itile]) / H) * chunk;
         const int64_t last = min((int64_t)a.near_cnt[itile], first + chunk);
         const SimDesc d = a.sims[sim_of_tile(a.sims, a.nsims, itile)];
         const uint32_t *row = a.nearbits + d.bits_off + (itile - d.tile_off) * d.words;
 
         const float4 ci = a.tbox_c[itile];
         const float4 ei = a.tbox_e[itile];
-        const int64_t ibase = itile * T + lane * KI;
+        const int64_t ibase = itile * T + half * 32 * TI + lane * TI;
         float2 xi[NPAIR], yi[NPAIR], zi[NPAIR], rxi[NPAIR], ryi[NPAIR], rzi[NPAIR], hI[NPAIR];
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
@@ -732,7 +748,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
         if (jt >= 0) issue(d.tile_off + jt, b);
         for (int64_t rk = first; rk < last && jt >= 0; ++rk) {
             const int64_t jn = (rk + 1 < last) ? next_near(row, d.words, jt + 1, lane) : -1;
-            if (jn >= 0) issue(d.tile_off + jn, b ^ 1);
+            if (NB == 2 && jn >= 0) issue(d.tile_off + jn, b ^ 1);
             bool got = true;
             if (lane == 0) got = mbar_wait_bounded(smem_u32(&bars[b]), (uint32_t)(uses[b] & 1), a.wait_ns);
             if (!__shfl_sync(0xffffffffu, got, 0)) {
@@ -740,7 +756,7 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
                     atomicExch(a.err, (int)STEPS_ETIMEOUT);
                     // drain the copies still in flight before the warp exits
                     mbar_wait_bounded(smem_u32(&bars[b]), (uint32_t)(uses[b] & 1), kDrainNs);
-                    if (jn >= 0)
+                    if (NB == 2 && jn >= 0)
                         mbar_wait_bounded(smem_u32(&bars[b ^ 1]), (uint32_t)(uses[b ^ 1] & 1), kDrainNs);
                 }
                 return;
@@ -782,24 +798,39 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
                 soft = soft || gap2 <= __fmul_rn(hs, hs);
             }
             if (soft)
-                near_tile_terms<KI, COMP, FOLD, true>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
+                near_tile_terms<TI, COMP, FOLD, true, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
                                                       cz_);
             else
-                near_tile_terms<KI, COMP, FOLD, false>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
+                near_tile_terms<TI, COMP, FOLD, false, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
                                                        cz_);
             __syncwarp();  // every lane is done with buffer b before it is refilled
             jt = jn;
-            b ^= 1;
+            if (NB == 2)
+                b ^= 1;
+            else if (jn >= 0)
+                issue(d.tile_off + jn, b);
         }
         double *P = a.item_part + (size_t)item * 3 * T;
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
 #pragma unroll
             for (int e = 0; e < 2; ++e) {
-                const int li = lane * KI + 2 * q + e;
+                const int li = half * 32 * TI + lane * TI + 2 * q + e;
                 P[li] = (double)(e ? hx[q].y : hx[q].x) + (double)(e ? cx_[q].y : cx_[q].x);
                 P[T + li] = (double)(e ? hy[q].y : hy[q].x) + (double)(e ? cy_[q].y : cy_[q].x);
                 P[2 * T + li] = (double)(e ? hz[q].y : hz[q].x) + (double)(e ? cz_[q].y : cz_[q].x);
+            }
+        }
+        // the other halves of the tile are another item's: zero here
+#pragma unroll
+        for (int hh = 0; hh < H; ++hh) {
+            if (hh == half) continue;
+#pragma unroll
+            for (int t = 0; t < TI; ++t) {
+                const int li = hh * 32 * TI + lane * TI + t;
+                P[li] = 0.0;
+                P[T + li] = 0.0;
+                P[2 * T + li] = 0.0;
             }
         }
     }
@@ -867,7 +898,7 @@ constexpr size_t smem_of() {
 
 template <int KI>
 constexpr size_t near_smem_of() {
-    return (size_t)kNearWarps * 2 * (32 * KI) * 64 + 2 * kNearWarps * sizeof(uint64_t);
+    return (size_t)kNearWarps * near_buffers<KI>() * (32 * KI) * 64 + 2 * kNearWarps * sizeof(uint64_t);
 }
 
 struct VariantImpl {
@@ -898,7 +929,7 @@ const VariantImpl kVariants[] = {
     STEPS_VARIANT(4, 8, 4, false, 32, 2, 2, false, false, "naive_ki4_w8_u2"),
     STEPS_VARIANT(2, 8, 4, false, 32, 4, 4, false, false, "naive_ki2_w8_u4"),
     // symmetric far field (force_sym.cu): 256-particle tiles, 4 compute warps
-    {{8, 4, 2, true, "sym_ki8_w4", 2}, nullptr, near_f32_kernel<8, true, kNearFold>, 0, near_smem_of<8>()},
+    {{8, 4, 4, true, "sym_ki8_w4", 2, 3}, nullptr, near_f32_kernel<8, true, kNearFold>, 0, near_smem_of<8>()},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -907,7 +938,7 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 int num_variants() { return kNumVariants; }
 const Variant &variant(int k) { return kVariants[k].v; }
 size_t force_smem_bytes(int k) {
-    return kVariants[k].v.form == 2 ? sym_smem_bytes(kVariants[k].v.W, kVariants[k].v.NS) : kVariants[k].smem;
+    return kVariants[k].v.form == 2 ? sym_smem_bytes(kVariants[k].v.W) : kVariants[k].smem;
 }
 
 ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const SimDesc *dev_sims,
@@ -940,7 +971,7 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
     cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
     if (sym) {
         // persistent grid; every unit adds to fixed-point sums, no per-CTA partials
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(W, vi.v.NS),
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(W, vi.v.ctas),
                                                                     units));
         p.grid = (int)grid;
         p.smax = 0;
@@ -1022,7 +1053,8 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     }
     near_count_kernel<<<(unsigned)((s.ntile * 32 + 255) / 256), 256, 0, st>>>(nr.bits, p.sims, p.nsims,
                                                                              s.ntile, nr.cnt);
-    near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, nr.item_off, nr.meta);
+    near_scan_kernel<<<1, 1024, 0, st>>>(nr.cnt, s.ntile, nr.cap_items, vi.v.KI == 8 ? 2 : 1,
+                                         nr.item_off, nr.meta);
     int per_sm = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, vi.near_fn, 32 * kNearWarps, vi.near_smem) !=
             cudaSuccess || per_sm < 1)

@@ -7,7 +7,9 @@
 // (I < J) once and adds the pair's force to both particles: per pair the
 // separation (3), r^2 (3), MUFU rsqrt, 1/r^3 (2), and two scaled
 // accumulations (1 + 3 each) -- 16 FP32 lane operations and one MUFU for two
-// interactions, against 20 and two for evaluating each order separately.
+// interactions, against 20 and two for evaluating each order separately
+// (plus 3 additions per pair for the exact separation and 3 per source and
+// step that bound the rounding of the source-side sums).
 //
 // Work layout (GB300-first):
 //  * Tiles of T = 256 Morton-ordered particles with FP32 offsets from an FP32
@@ -16,10 +18,10 @@
 //    shift dc = c_I - c_J.
 //  * A unit is (target block b of W tiles, source tile J) with J after the
 //    block; pairs of tiles inside one block go to the near-field kernel.  A
-//    persistent grid splits the units evenly (stream-K); a producer warp
-//    streams source tiles into a shared-memory ring with TMA bulk copies
-//    (cp.async.bulk completing on mbarriers); compute warp w owns target tile
-//    b W + w.
+//    persistent grid splits the units evenly (stream-K); source tiles stream
+//    into a shared-memory ring with TMA bulk copies (cp.async.bulk completing
+//    on mbarriers), each stage refilled by the last warp done with it; warp w
+//    owns target tile b W + w.
 //  * Inside a warp, lane l holds 8 targets (particles l + 32 t) as 4 packed
 //    pairs (FFMA2).  The source tile is processed in 4 rounds of 32 steps; at
 //    step s lane l takes the 2 sources of group (l + s) mod 32, so no two
@@ -27,13 +29,13 @@
 //    the group from lane to lane by one shuffle per step.  After a round each
 //    lane holds the complete contribution of the warp's 256 targets to its own
 //    group's sources.
+//  * The separation is (o_j - o_i) - (c_I - c_J): offsets first (both at tile
+//    scale), then the exact centre difference, so every rounding is relative
+//    to the pair's own separation and varies from pair to pair.
 //  * Target sums: FP32 partials over 32 sources folded into a per-target
-//    compensated (Kahan) pair kept in shared memory.  The rounding of the
-//    target position relative to the source tile centre, s = fl(o_i + dc), is
-//    the same for all sources of a unit and is undone to first order with
-//    the source tile's monopole tidal tensor (its exact value comes from
-//    Fast2Sum).  For the source side the per-target roundings are independent
-//    and average out.
+//    compensated (Kahan) pair kept in shared memory.  Source sums: a fresh
+//    partial of the step's 8 targets added once per step to the group's
+//    running sum (32 additions per round).
 //  * Both sides are accumulated in 64-bit fixed point with red.global.add:
 //    every partial is scaled by a per-tile power of two, chosen from a bound
 //    on the tile's far-field sum computed by the classification pass, and
@@ -41,8 +43,8 @@
 //    does not depend on the order of the atomic adds: evaluations are
 //    bit-for-bit reproducible.
 //  * Every mbarrier wait is bounded (%globaltimer); a wait that runs out
-//    records STEPS_ETIMEOUT, the producer drains its own copies and the CTA
-//    exits.
+//    records STEPS_ETIMEOUT, the warp waits (bounded) for the copies issued so
+//    far and exits.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -126,53 +128,30 @@ __device__ __forceinline__ void red_fixed(unsigned long long *addr, float v, flo
 }
 
 // One far unit for this warp: the warp's 256 targets against the 256 sources
-// of the staged tile S.  meta = (dc, M_J).  Target sums go to the Kahan state
-// myk; source sums to the fixed-point array (scale scJ) of the source tile
-// starting at particle jbase.
+// of the staged tile S.  meta = (dc = c_I - c_J, M_J); myio holds the
+// negated target offsets.  Target sums go to the Kahan state myk; source sums
+// to the fixed-point array (scale scJ) of the source tile starting at
+// particle jbase.
 template <int UNR>
 __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const float4 meta,
                                              const float2 *__restrict__ myio, float4 *__restrict__ myk,
                                              const float2 (&mi)[kNP], int lane, int64_t jbase, float scJ,
                                              unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
-    const float2 neg1 = make_float2(-1.0f, -1.0f);
-    float2 nsx[kNP], nsy[kNP], nsz[kNP];  // -s, s = fl(o_i + dc): target relative to the source tile centre
-    float2 px[kNP], py[kNP], pz[kNP];     // FP32 target partials (the first starts at the shift correction)
-    {
-        const float2 dcx2 = make_float2(meta.x, meta.x), dcy2 = make_float2(meta.y, meta.y),
-                     dcz2 = make_float2(meta.z, meta.z);
-        const float2 ndx = make_float2(-meta.x, -meta.x), ndy = make_float2(-meta.y, -meta.y),
-                     ndz = make_float2(-meta.z, -meta.z);
-        const float2 M2 = make_float2(meta.w, meta.w);
+    // The separation is formed as (o_j - o_i) - dc: the offsets are small (tile
+    // scale) and dc is exact, so d carries only rounding relative to itself.
+    // (Forming a shifted target s = o_i + dc once per unit would save one
+    // addition, but its rounding acts as a shift of the target that is the same
+    // for all its sources: a coherent error that does not average out.)
+    float2 nox[kNP], noy[kNP], noz[kNP];  // -o_i
+    float2 px[kNP], py[kNP], pz[kNP];     // FP32 target partials
+    const float2 ndx = make_float2(-meta.x, -meta.x), ndy = make_float2(-meta.y, -meta.y),
+                 ndz = make_float2(-meta.z, -meta.z);
 #pragma unroll
-        for (int q = 0; q < kNP; ++q) {
-            const float2 ox = myio[(0 * kNP + q) * 32 + lane];
-            const float2 oy = myio[(1 * kNP + q) * 32 + lane];
-            const float2 oz = myio[(2 * kNP + q) * 32 + lane];
-            nsx[q] = __ffma2_rn(ox, neg1, ndx);
-            nsy[q] = __ffma2_rn(oy, neg1, ndy);
-            nsz[q] = __ffma2_rn(oz, neg1, ndz);
-            // l = (o_i + dc) - s exactly (Fast2Sum: |dc| > |o_i| for every far pair)
-            const float2 lx = __fadd2_rn(ox, __fadd2_rn(nsx[q], dcx2));
-            const float2 ly = __fadd2_rn(oy, __fadd2_rn(nsy[q], dcy2));
-            const float2 lz = __fadd2_rn(oz, __fadd2_rn(nsz[q], dcz2));
-            // The true target sits at s + l: first-order change of the source
-            // tile's monopole field M (-x)/|x|^3 at x = s,
-            //   -M l/R^3 + 3 M s (s.l)/R^5,  R = |s|.
-            float2 R2 = __fmul2_rn(nsx[q], nsx[q]);
-            R2 = __ffma2_rn(nsy[q], nsy[q], R2);
-            R2 = __ffma2_rn(nsz[q], nsz[q], R2);
-            const float2 Ri = make_float2(rsqrt_approx(R2.x), rsqrt_approx(R2.y));
-            const float2 Ri2 = __fmul2_rn(Ri, Ri);
-            const float2 k1 = __fmul2_rn(__fmul2_rn(M2, Ri), Ri2);
-            float2 proj = __fmul2_rn(nsx[q], lx);
-            proj = __ffma2_rn(nsy[q], ly, proj);
-            proj = __ffma2_rn(nsz[q], lz, proj);
-            const float2 k2 = __fmul2_rn(__fmul2_rn(make_float2(3.f, 3.f), k1), __fmul2_rn(proj, Ri2));
-            const float2 nk1 = __fmul2_rn(k1, neg1);
-            px[q] = __ffma2_rn(k2, nsx[q], __fmul2_rn(nk1, lx));
-            py[q] = __ffma2_rn(k2, nsy[q], __fmul2_rn(nk1, ly));
-            pz[q] = __ffma2_rn(k2, nsz[q], __fmul2_rn(nk1, lz));
-        }
+    for (int q = 0; q < kNP; ++q) {
+        nox[q] = myio[(0 * kNP + q) * 32 + lane];
+        noy[q] = myio[(1 * kNP + q) * 32 + lane];
+        noz[q] = myio[(2 * kNP + q) * 32 + lane];
+        px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
     }
     const int from = (lane + 1) & 31;
 #pragma unroll 1
@@ -191,11 +170,15 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
                     const float4 A = src[0], B = src[32];
                     const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
                     const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+                    // this step's 8 targets on the two sources form a fresh partial that is
+                    // added to the group's running sum once: the sum grows by 32 additions
+                    // per round instead of 128 (its rounding grows with the additions)
+                    float2 tx, ty, tz;
 #pragma unroll
                     for (int q = 0; q < kNP; ++q) {
-                        const float2 dx = __fadd2_rn(xj, nsx[q]);  // x_j - x_i
-                        const float2 dy = __fadd2_rn(yj, nsy[q]);
-                        const float2 dz = __fadd2_rn(zj, nsz[q]);
+                        const float2 dx = __fadd2_rn(__fadd2_rn(xj, nox[q]), ndx);  // x_j - x_i
+                        const float2 dy = __fadd2_rn(__fadd2_rn(yj, noy[q]), ndy);
+                        const float2 dz = __fadd2_rn(__fadd2_rn(zj, noz[q]), ndz);
                         float2 r2 = __fmul2_rn(dx, dx);
                         r2 = __ffma2_rn(dy, dy, r2);
                         r2 = __ffma2_rn(dz, dz, r2);
@@ -206,10 +189,19 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
                         py[q] = __ffma2_rn(si, dy, py[q]);
                         pz[q] = __ffma2_rn(si, dz, pz[q]);
                         const float2 sj = __fmul2_rn(u, mi[q]);
-                        Sx[k] = __ffma2_rn(sj, dx, Sx[k]);
-                        Sy[k] = __ffma2_rn(sj, dy, Sy[k]);
-                        Sz[k] = __ffma2_rn(sj, dz, Sz[k]);
+                        if (q == 0) {
+                            tx = __fmul2_rn(sj, dx);
+                            ty = __fmul2_rn(sj, dy);
+                            tz = __fmul2_rn(sj, dz);
+                        } else {
+                            tx = __ffma2_rn(sj, dx, tx);
+                            ty = __ffma2_rn(sj, dy, ty);
+                            tz = __ffma2_rn(sj, dz, tz);
+                        }
                     }
+                    Sx[k] = __fadd2_rn(Sx[k], tx);
+                    Sy[k] = __fadd2_rn(Sy[k], ty);
+                    Sz[k] = __fadd2_rn(Sz[k], tz);
                 }
                 // pass the group's sums on: lane l takes over group (l + st + 1) mod 32
 #pragma unroll
@@ -251,15 +243,52 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
     }
 }
 
-template <int W, int NS, int MINB, int UNR>
-__global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymArgs a) {
+// Fill stage s = k mod NS with unit k of this CTA's range (cursor c): the W
+// warps' metadata (dc, M_J or -1 when that warp's tile pair is near) and the
+// bulk copy of the source tile.  Called by one whole warp.
+template <int W, int NS>
+__device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> &c, int64_t k, float4 *sj,
+                                          float4 *smeta, uint64_t *full, long long *issued, int lane) {
     constexpr uint32_t BYTES_J = kT * 32u;
+    const int s = (int)(k % NS);
+    const int64_t jg = c.d.tile_off + c.J;
+    if (lane < W) {
+        const int64_t il = c.b * W + lane;
+        const uint32_t word = a.nearbits[c.d.bits_off + il * c.d.words + (c.J >> 5)];
+        const bool near = (word >> (c.J & 31)) & 1u;
+        const float4 ci = a.tbox_c[c.d.tile_off + il], cj = a.tbox_c[jg];
+        // exact: the tile centres lie on a common grid (staging)
+        smeta[s * W + lane] = make_float4(__fsub_rn(ci.x, cj.x), __fsub_rn(ci.y, cj.y), __fsub_rn(ci.z, cj.z),
+                                          near ? -1.f : a.tbox_e[jg].w);
+    }
+    __syncwarp();
+    if (lane == 0) {
+        issued[s] = k;
+        __threadfence_block();  // the metadata before the release-arrive
+        // every warp's reads of the stage's previous tile before the async-proxy write
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_arrive_expect_tx(fb, BYTES_J);
+        bulk_g2s(smem_u32(sj + (size_t)s * 2 * kT), a.sdup + jg * 2 * kT, BYTES_J, fb);
+    }
+}
+
+// The CTA's W warps share an NS-stage ring of source tiles.  There is no
+// producer warp: warp 0 fills the first NS stages, and afterwards the last
+// warp done with a stage (a shared-memory counter) refills it with the unit
+// NS further on, so every warp of the CTA computes.  (Measured against a
+// dedicated producer warp: the same speed at equal compute warps, and the
+// producer's registers go to a third CTA per SM.)
+template <int W, int NS, int MINB, int UNR>
+__global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
-    float4 *sj = reinterpret_cast<float4 *>(smem);                         // [NS][2 kT] source tiles
-    float4 *smeta = sj + NS * 2 * kT;                                      // [NS][W] (dc, M_J or -1: near)
-    float2 *sio = reinterpret_cast<float2 *>(smeta + NS * W);              // [W][3][kNP][32] target offsets
-    float4 *skah = reinterpret_cast<float4 *>(sio + W * 3 * kNP * 32);     // [W][3][kNP][32] Kahan (hi, -c)
-    uint64_t *bars = reinterpret_cast<uint64_t *>(skah + W * 3 * kNP * 32);  // full[NS], empty[NS]
+    float4 *sj = reinterpret_cast<float4 *>(smem);                          // [NS][2 kT] source tiles
+    float4 *smeta = sj + NS * 2 * kT;                                       // [NS][W] (dc, M_J or -1: near)
+    float2 *sio = reinterpret_cast<float2 *>(smeta + NS * W);               // [W][3][kNP][32] -(target offsets)
+    float4 *skah = reinterpret_cast<float4 *>(sio + W * 3 * kNP * 32);      // [W][3][kNP][32] Kahan (hi, -c)
+    uint64_t *full = reinterpret_cast<uint64_t *>(skah + W * 3 * kNP * 32); // [NS]
+    long long *issued = reinterpret_cast<long long *>(full + NS);          // [NS] last unit copied into a stage
+    int *done = reinterpret_cast<int *>(issued + NS);                       // [NS] warps finished with a stage
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -271,66 +300,27 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymAr
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
-            mbar_init(smem_u32(&bars[s]), 1);
-            mbar_init(smem_u32(&bars[NS + s]), W);
+            mbar_init(smem_u32(&full[s]), 1);
+            issued[s] = -1;
+            done[s] = 0;
         }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
     if (count <= 0) return;
 
-    if (warp == W) {
-        // ---------------- producer warp ----------------
-        UnitCursor<W> c;
-        c.locate(a.sims, a.nsims, u0);
-        int64_t k = 0;
-        bool ok = true;
-        for (; k < count; ++k) {
-            const int s = (int)(k % NS);
-            if (k >= NS) {
-                bool got = true;
-                if (lane == 0)
-                    got = mbar_wait_bounded(smem_u32(&bars[NS + s]), (uint32_t)(((k / NS) - 1) & 1), a.wait_ns);
-                if (!__shfl_sync(0xffffffffu, got, 0)) {
-                    ok = false;
-                    break;
-                }
-            }
-            const int64_t jg = c.d.tile_off + c.J;
-            if (lane < W) {
-                const int64_t il = c.b * W + lane;
-                const uint32_t word = a.nearbits[c.d.bits_off + il * c.d.words + (c.J >> 5)];
-                const bool near = (word >> (c.J & 31)) & 1u;
-                const float4 ci = a.tbox_c[c.d.tile_off + il], cj = a.tbox_c[jg];
-                // exact: the tile centres lie on a common grid (staging)
-                smeta[s * W + lane] = make_float4(__fsub_rn(ci.x, cj.x), __fsub_rn(ci.y, cj.y),
-                                                  __fsub_rn(ci.z, cj.z), near ? -1.f : a.tbox_e[jg].w);
-            }
-            __syncwarp();
-            if (lane == 0) {
-                __threadfence_block();  // the other lanes' metadata before the release-arrive
-                const uint32_t full = smem_u32(&bars[s]);
-                mbar_arrive_expect_tx(full, BYTES_J);
-                bulk_g2s(smem_u32(sj + (size_t)s * 2 * kT), a.sdup + jg * 2 * kT, BYTES_J, full);
-            }
-            c.next(a.sims, a.nsims);
-        }
-        if (lane == 0) {
-            if (!ok) atomicExch(a.err, (int)STEPS_ETIMEOUT);
-            // drain: every copy this warp issued must land before the CTA may exit
-            const int64_t first = k > NS ? k - NS : 0;
-            for (int64_t q = first; q < k; ++q)
-                if (!mbar_wait_bounded(smem_u32(&bars[q % NS]), (uint32_t)((q / NS) & 1), kDrainNs))
-                    atomicExch(a.err, (int)STEPS_ETIMEOUT);
-        }
-        return;
-    }
-
-    // ---------------- compute warps ----------------
-    float2 *myio = sio + warp * 3 * kNP * 32;
-    float4 *myk = skah + warp * 3 * kNP * 32;
     UnitCursor<W> c;
     c.locate(a.sims, a.nsims, u0);
+    if (warp == 0) {
+        UnitCursor<W> p = c;
+        for (int64_t k = 0; k < NS && k < count; ++k) {
+            sym_issue<W, NS>(a, p, k, sj, smeta, full, issued, lane);
+            p.next(a.sims, a.nsims);
+        }
+    }
+
+    float2 *myio = sio + warp * 3 * kNP * 32;
+    float4 *myk = skah + warp * 3 * kNP * 32;
     int64_t u = u0;
     int64_t k = 0;
     while (u < u1) {
@@ -343,9 +333,9 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymAr
             const float4 *p0 = a.sdup + (ig * kKI + 2 * q) * 64 + lane;  // particle 64 q + lane
             const float4 *p1 = p0 + 64;                                   // particle 64 q + 32 + lane
             const float4 A0 = p0[0], B0 = p0[32], A1 = p1[0], B1 = p1[32];
-            myio[(0 * kNP + q) * 32 + lane] = make_float2(A0.x, A1.x);
-            myio[(1 * kNP + q) * 32 + lane] = make_float2(A0.z, A1.z);
-            myio[(2 * kNP + q) * 32 + lane] = make_float2(B0.x, B1.x);
+            myio[(0 * kNP + q) * 32 + lane] = make_float2(-A0.x, -A1.x);
+            myio[(1 * kNP + q) * 32 + lane] = make_float2(-A0.z, -A1.z);
+            myio[(2 * kNP + q) * 32 + lane] = make_float2(-B0.x, -B1.x);
             mi[q] = make_float2(B0.z, B1.z);
 #pragma unroll
             for (int cc = 0; cc < 3; ++cc) myk[(cc * kNP + q) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -353,8 +343,15 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymAr
         __syncwarp();
         for (; u < seg_end; ++u, ++k) {
             const int s = (int)(k % NS);
-            if (!mbar_wait_bounded(smem_u32(&bars[s]), (uint32_t)((k / NS) & 1), a.wait_ns)) {
-                if (lane == 0) atomicExch(a.err, (int)STEPS_ETIMEOUT);
+            if (!mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NS) & 1), a.wait_ns)) {
+                if (lane == 0) {
+                    atomicExch(a.err, (int)STEPS_ETIMEOUT);
+                    // drain the copies issued so far before the warp leaves
+                    for (int t = 0; t < NS; ++t) {
+                        const long long q = ((volatile long long *)issued)[t];
+                        if (q >= 0) mbar_wait_bounded(smem_u32(&full[t]), (uint32_t)((q / NS) & 1), kDrainNs);
+                    }
+                }
                 return;
             }
             const float4 meta = smeta[s * W + warp];
@@ -363,9 +360,19 @@ __global__ void __launch_bounds__((W + 1) * 32, MINB) sym_far_kernel(const SymAr
                 sym_far_unit<UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT, a.tscale[jg],
                                   a.acc, a.np, a.nonfinite);
             }
-            // release the stage so the producer can refill it
+            // done with the stage: the last warp refills it with unit k + NS
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(&bars[NS + s]));
+            int last = 0;
+            if (lane == 0) {
+                __threadfence_block();
+                last = atomicAdd(&done[s], 1) == W - 1;
+                if (last) done[s] = 0;
+            }
+            if (__shfl_sync(0xffffffffu, last, 0) && k + NS < count) {
+                UnitCursor<W> p = c;
+                for (int t = 0; t < NS; ++t) p.next(a.sims, a.nsims);
+                sym_issue<W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
+            }
             c.next(a.sims, a.nsims);
         }
         // ---- segment done: this warp's target sums into the fixed-point array ----
@@ -468,22 +475,20 @@ __global__ void sym_fixup_kernel(const unsigned long long *__restrict__ acc, int
     if (nonfinite && (!isfinite(sx) || !isfinite(sy) || !isfinite(sz))) *nonfinite = 1;
 }
 
-constexpr int kNS = 2;
-constexpr int kUNR = 2;
+constexpr int kNS = 4;   // stages of the source-tile ring
+constexpr int kUNR = 4;  // steps unrolled
 
 template <int W>
 constexpr size_t sym_smem_of() {
     return (size_t)kNS * 2 * kT * 16 + (size_t)kNS * W * 16 + (size_t)W * 3 * kNP * 32 * 8 +
-           (size_t)W * 3 * kNP * 32 * 16 + 2 * kNS * sizeof(uint64_t);
+           (size_t)W * 3 * kNP * 32 * 16 + kNS * (sizeof(uint64_t) + sizeof(long long) + sizeof(int));
 }
 
 using SymFn = void (*)(const SymArgs);
 
-SymFn sym_fn(int W) {
-    switch (W) {
-        case 4: return sym_far_kernel<4, kNS, 3, kUNR>;
-        default: return nullptr;
-    }
+SymFn sym_fn(int W, int ctas) {
+    if (W != 4 || ctas != 3) return nullptr;
+    return sym_far_kernel<4, kNS, 3, kUNR>;
 }
 
 }  // namespace
@@ -493,18 +498,15 @@ int64_t sym_units(int64_t ntile, int W) {
     return nb >= 1 ? (nb - 1) * ntile - (int64_t)W * (nb - 1) * nb / 2 : 0;
 }
 
-size_t sym_smem_bytes(int W, int NS) {
-    (void)NS;
-    return W == 4 ? sym_smem_of<4>() : 0;
-}
+size_t sym_smem_bytes(int W) { return W == 4 ? sym_smem_of<4>() : 0; }
 
-int sym_blocks_per_sm(int W, int NS) {
-    SymFn fn = sym_fn(W);
+int sym_blocks_per_sm(int W, int ctas) {
+    SymFn fn = sym_fn(W, ctas);
     if (!fn) return 0;
-    const size_t smem = sym_smem_bytes(W, NS);
+    const size_t smem = sym_smem_bytes(W);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, (W + 1) * 32, smem) != cudaSuccess || per < 1)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, W * 32, smem) != cudaSuccess || per < 1)
         per = 1;
     return per;
 }
@@ -522,7 +524,7 @@ cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const Near
 cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScratch &nr, int *err,
                            long long wait_ns, cudaStream_t st) {
     const int W = variant(p.variant).W;
-    SymFn fn = sym_fn(W);
+    SymFn fn = sym_fn(W, variant(p.variant).ctas);
     if (!fn) return cudaErrorInvalidValue;
     SymArgs a;
     a.sdup = s.sdup;
@@ -539,7 +541,7 @@ cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScrat
     a.units = p.units;
     a.wait_ns = wait_ns;
     if (p.units <= 0) return cudaSuccess;
-    fn<<<p.grid, (W + 1) * 32, sym_smem_bytes(W, kNS), st>>>(a);
+    fn<<<p.grid, W * 32, sym_smem_bytes(W), st>>>(a);
     return cudaGetLastError();
 }
 

@@ -49,6 +49,9 @@ struct Variant {
     // particles (explicit separation, 8 lane operations and half an MUFU per
     // interaction; reads Staging::sdup, accumulates in fixed point)
     int form;
+    // symmetric kernel: CTAs of 4 warps per SM it is compiled for (3: up to
+    // 168 registers per thread)
+    int ctas = 0;
 };
 
 int num_variants();
@@ -130,8 +133,9 @@ ForcePlan plan_force(const Staging &s, int variant, int num_sms);
 // source tile J) with J >= (b + 1) W, per system; pairs of tiles inside one
 // block go to the near field.
 int64_t sym_units(int64_t ntile, int W);
-size_t sym_smem_bytes(int W, int NS);
-int sym_blocks_per_sm(int W, int NS);
+size_t sym_smem_bytes(int W);
+// ctas: the variant's Variant::ctas (which compiled kernel)
+int sym_blocks_per_sm(int W, int ctas);
 // Near bitmap (all ordered tile pairs; same-block pairs are near), per-tile
 // fixed-point scales from a bound on the far-field sums, near/all counts.
 cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const NearScratch &nr, float alpha,
