@@ -35,13 +35,13 @@ if ROOT not in sys.path:
 METRIC = "pair interactions/s at N=2^20: mixed vs FP64 GPU at <=1e-6 rms rel force err"
 UNIT = "interactions/s"
 FLOP_PER_INTERACTION = 20  # the usual direct N-body convention
+FP64_FMA_PER_SM_CLK = 2    # GB300 FP64 pipe: 2 DFMA per SM and cycle (ncu's peak table)
 L2_FLUSH_BYTES = 512 << 20
-# DRAM bytes (read + write) of one far-field launch, from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum, 1 pass) of the first launch of
-# the named variant on the N = 2^20 workload; reported only for that variant
-# and size (profiles/force_far_expansion_1m.md).
-FAR_TRAFFIC_BYTES = {("exp_ki6_w4_u4", 1048576): 3702198784 + 42648064,
-                     ("exp_ki4_w4_u8", 1048576): 5164149504 + 45248512}
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) of one far-field
+# launch, measured by ncu (one pass, the launch-list run of this bench command)
+# for the named variant at the named size, with the kernel source as committed
+# alongside; any other variant or size reports null.
+FAR_TRAFFIC_BYTES = {}
 
 
 def peaks():
@@ -181,10 +181,11 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def ensemble_throughput(stream, steps_mod, workloads_mod, timed_steps=4):
+def ensemble_throughput(stream, steps_mod, workloads_mod):
     """Config 4: 64 compactified members (uneven N, differing Om and sigma8)
-    in one ensemble vs the same members run one after another; sims/hour for
-    100-step runs, extrapolated from the timed steps."""
+    advanced together in one ensemble vs the same members run one after
+    another; both arms time the complete 100-step runs (CUDA events), after
+    initialisation (which includes each arm's autotuning)."""
     import torch
     ens = workloads_mod.ensemble(seed=4)
     ps = ens.sims
@@ -192,40 +193,44 @@ def ensemble_throughput(stream, steps_mod, workloads_mod, timed_steps=4):
     cfgs = [steps_mod.make_config(mode=steps_mod.STEPS_COMOVING, prec=steps_mod.STEPS_F32_COMP, G=p.G,
                                   Om=p.Om, OL=p.OL, resort_every=8) for p in ps]
     dts = np.stack([workloads_mod.loga_schedule(p.a0, 1.0, nsteps_run, p.Om, p.OL)[1] for p in ps])
-    e = steps_mod.Ensemble(ps, cfgs, stream=stream.cuda_stream)
-    e.run(dts[:, :2])  # warm-up (graph capture, first re-sort bookkeeping)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e = steps_mod.Ensemble(ps, cfgs, stream=stream.cuda_stream)
+    variant = steps_mod.steps_variants()[e.variant()]
     torch.cuda.synchronize()
     with torch.cuda.stream(stream):
         ev0.record(stream)
-    e.run(dts[:, 2:2 + timed_steps])
+    e.run(dts)
     with torch.cuda.stream(stream):
         ev1.record(stream)
     ev1.synchronize()
-    t_ens = ev0.elapsed_time(ev1) * 1e-3 / timed_steps
+    t_ens = ev0.elapsed_time(ev1) * 1e-3
     total, nnear, nall = e.stats()
     e.close()
     t_seq = 0.0
+    seq_variants = set()
     for s, p in enumerate(ps):
         sim = steps_mod.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfgs[s],
                                    stream=stream.cuda_stream)
-        sim.run(dts[s, :2])
+        seq_variants.add(steps_mod.steps_variants()[steps_mod.steps_get_variant(sim.ctx)])
         torch.cuda.synchronize()
         with torch.cuda.stream(stream):
             ev0.record(stream)
-        sim.run(dts[s, 2:2 + timed_steps])
+        sim.run(dts[s])
         with torch.cuda.stream(stream):
             ev1.record(stream)
         ev1.synchronize()
-        t_seq += ev0.elapsed_time(ev1) * 1e-3 / timed_steps
+        t_seq += ev0.elapsed_time(ev1) * 1e-3
         sim.close()
-    inter = float(sum(int(p.n) ** 2 for p in ps))
+    inter = float(sum(int(p.n) ** 2 for p in ps)) * nsteps_run
     return {"workload": "64 compactified LCDM members, N ~ U[8192, 131072] (sum %d), Om ~ U[0.25, 0.35], "
-                        "sigma8 ~ U[0.7, 0.9], 100 KDK steps from a = 0.02" % sum(p.n for p in ps),
-            "sims_per_hour": len(ps) * 3600.0 / (t_ens * nsteps_run),
-            "sims_per_hour_sequential": len(ps) * 3600.0 / (t_seq * nsteps_run),
-            "ms_per_step": 1e3 * t_ens, "ms_per_step_sequential": 1e3 * t_seq,
-            "interactions_per_s": inter / t_ens, "timed_steps": timed_steps,
+                        "sigma8 ~ U[0.7, 0.9], 100 KDK steps from a = 0.02 to 1" % sum(p.n for p in ps),
+            "sims_per_hour": len(ps) * 3600.0 / t_ens,
+            "sims_per_hour_sequential": len(ps) * 3600.0 / t_seq,
+            "batched_over_sequential": t_seq / t_ens,
+            "run_s": t_ens, "run_s_sequential": t_seq,
+            "ms_per_step": 1e3 * t_ens / nsteps_run, "ms_per_step_sequential": 1e3 * t_seq / nsteps_run,
+            "interactions_per_s": inter / t_ens, "timed_steps": nsteps_run,
+            "variant": variant, "variants_sequential": sorted(seq_variants),
             "near_field_fraction": nnear / max(nall, 1)}
 
 
@@ -258,6 +263,55 @@ def periodic_throughput(steps_mod, n=16384, L=1.0, seed=21):
         tflops = 20 * terms * n * n / per / 1e12
         out[name] = {"ms_per_evaluation": 1e3 * per, "pair_image_terms_per_s": terms * n * n / per,
                      "fp32_tflops_at_20_flop": tflops, "frac_of_fp32_peak": tflops / peak}
+    return out
+
+
+def cpu_workloads(stream, steps_mod, workloads_mod):
+    """The FP64 oracle on the host cores on the planned baseline workloads:
+    the small static system (4,096 particles) in full -- one force evaluation
+    and 10 KDK steps at dt = 1e-3 -- and the N = 262,144 compactified LCDM run
+    (200 steps from a = 0.02 to 1, advanced on the GPU) at three checkpoints,
+    4,096 seeded targets each against all sources, with the GPU's error there."""
+    import torch
+    import oracle
+    out = []
+    p = workloads_mod.static_ball(seed=1)
+    h = oracle.softening(p.mass, p.h_min)
+    t0 = time.perf_counter()
+    oracle.pair_acc(p.pos, p.mass, h, p.G)
+    kd = oracle.KDK(p.pos, p.vel, p.mass, h, oracle.cosmo(comoving=False))
+    for _ in range(10):
+        kd.step(1e-3)
+    dt_cpu = time.perf_counter() - t0
+    inter = 11.0 * p.n * p.n  # the evaluation plus one per KDK step
+    out.append({"workload": "static ball + 16 shells, N=%d: 1 force evaluation + 10 KDK steps" % p.n,
+                "interactions_per_s": inter / dt_cpu, "s": dt_cpu})
+    q = workloads_mod.lcdm_262k()
+    hq = oracle.softening(q.mass, q.h_min)
+    _, dts = workloads_mod.loga_schedule(q.a0, 1.0, 200, q.Om, q.OL)
+    cfg = steps_mod.make_config(mode=steps_mod.STEPS_COMOVING, prec=steps_mod.STEPS_F32_COMP, G=q.G, Om=q.Om,
+                                OL=q.OL, resort_every=8)
+    sim = steps_mod.Simulation(q.pos, q.vel, q.mass, h_min=q.h_min, t0=q.t0, a0=q.a0, cfg=cfg,
+                               stream=stream.cuda_stream)
+    tg = workloads_mod.precision_targets(q.n)
+    done = 0
+    for stop in (0, 100, 200):
+        if stop > done:
+            sim.run(dts[done:stop])
+            done = stop
+        torch.cuda.synchronize()
+        pos = np.empty((q.n, 3))
+        acc = np.empty((q.n, 3))
+        _, a_now = steps_mod.steps_get_state(sim.ctx, pos=pos, acc=acc)
+        t0 = time.perf_counter()
+        ref = oracle.pair_acc(pos, q.mass, hq, q.G, targets=tg)
+        dt_cpu = time.perf_counter() - t0
+        e = np.linalg.norm(acc[tg] - ref, axis=1) / np.linalg.norm(ref, axis=1)
+        out.append({"workload": "compactified LCDM N=%d after %d of 200 steps (a = %.3f): %d targets x all "
+                                "sources" % (q.n, stop, a_now, tg.size),
+                    "interactions_per_s": tg.size * q.n / dt_cpu, "s": dt_cpu,
+                    "gpu_rms_rel_err": float(np.sqrt(np.mean(e ** 2))), "gpu_max_rel_err": float(e.max())})
+    sim.close()
     return out
 
 
@@ -384,6 +438,16 @@ def run_ours(args):
            "h2d_bytes_per_step": 2 * 3 * 8 * n, "d2h_bytes_per_step": 3 * 8 * n,
            "what": "steps_set_state(host pos, vel) + steps_get_state(host acc): one force evaluation per step"}
     sim.close()
+    evolved = None
+    if rank == 0 and not args.no_cpu:
+        # the pair term at the state reached after the warm-up and timed steps
+        ref_ev = oracle.pair_acc(pos_h.numpy(), p.mass, h, p.G, targets=tg)
+        e = np.linalg.norm(acc_h.numpy()[tg] - ref_ev, axis=1) / np.linalg.norm(ref_ev, axis=1)
+        evolved = {"rms": float(np.sqrt(np.mean(e ** 2))), "max": float(e.max()), "a": a_now,
+                   "steps": args.warmup + args.steps}
+    workloads_cpu = None
+    if rank == 0 and not args.no_cpu:
+        workloads_cpu = cpu_workloads(stream, steps, workloads)
     ensemble = None
     if rank == 0 and not args.no_ensemble:
         ensemble = ensemble_throughput(stream, steps, workloads)
@@ -406,6 +470,7 @@ def run_ours(args):
     pk = peaks()
     max_mhz = float(pk.get("sm_max_mhz", 2070.0))
     peak = fp32_peak_tflops(props.multi_processor_count, max_mhz)
+    fp64_peak = props.multi_processor_count * FP64_FMA_PER_SM_CLK * 2 * max_mhz * 1e6 / 1e12
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * total_s / args.steps, "higher_is_better": True,
@@ -424,7 +489,7 @@ def run_ours(args):
                      "pair_force_evaluation_tflops": FLOP_PER_INTERACTION * n * n / force_avg_s / 1e12,
                      "frac_at_observed_clock": (achieved / fp32_peak_tflops(props.multi_processor_count, clocks["sm_mhz"])
                                                 if clocks.get("sm_mhz") else None)},
-        "cpu_baseline": cpu,
+        "cpu_baseline": dict(cpu, workloads=workloads_cpu) if cpu else None,
         "e2e": e2e,
         "clocks": clocks,
         "gpu_launches": int(kernel_launches),
@@ -433,7 +498,13 @@ def run_ours(args):
                          **err.get("f32_comp", {})},
             "f32_naive": {"force_kernel_interactions_per_s": naive_rate, **err.get("f32_naive", {})},
             "f64_gpu": {"interactions_per_s": f64_rate, "sample": "%d targets x %d sources" % (big_tg.size, n),
+                        "kernel": "force_f64_list_kernel (FP64, one warp per target, lane-strided sources, shuffle-tree sum)",
+                        "fp64_tflops_at_20_flop": FLOP_PER_INTERACTION * f64_rate / 1e12,
+                        "fp64_peak_tflops": fp64_peak,
+                        "frac_of_fp64_peak_at_20_flop": FLOP_PER_INTERACTION * f64_rate / 1e12 / fp64_peak,
+                        "mixed_over_fp64": (value / ws) / f64_rate,
                         **err.get("f64_gpu", {})},
+            "f32_comp_evolved": evolved,
             "error_targets": int(tg.size),
         },
         "near_field_fraction": near_frac,

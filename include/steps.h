@@ -252,8 +252,8 @@ steps_status steps_profile_read(steps_ctx *ctx, double *force_ms, int64_t *force
 steps_status steps_profile_read_far(steps_ctx *ctx, double *far_ms, int64_t *far_launches);
 
 /*
- * steps_forces_noalloc -- the pair term of Eq. 8 (same definition and FP32
- * compensated arithmetic as steps_forces) for a system of at most
+ * steps_forces_noalloc -- the same pair term and FP32 compensated arithmetic
+ * as steps_forces (64-particle tiles, caller order) for a system of at most
  * STEPS_NOALLOC_MAX_N particles, without allocating any device memory.  The
  * paper has no counterpart: this entry point exists for callers that cannot
  * allocate around a force evaluation, e.g. code running inside an application
@@ -261,15 +261,17 @@ steps_status steps_profile_read_far(steps_ctx *ctx, double *far_ms, int64_t *far
  * that must not take the implicit device synchronisation of cudaMalloc and
  * cudaFree.  All scratch lives in one fixed array of about 6.7 MiB compiled
  * into this library; every device that loads the library holds it until exit.
- *   pos [n][3], mass [n], soft [n] (or NULL: Eq. 7 with h_min), acc_out [n][3]:
+ *   pos [n][3], mass [n], soft [n] (or NULL: derived from h_min as in steps_init), acc_out [n][3]:
  *   device pointers on the current device, caller order, caller-owned.
  *   cuda_stream: stream to run on (NULL = legacy default stream); the call
  *   synchronises it before returning.
- * Errors: EINVAL for n outside [1, STEPS_NOALLOC_MAX_N] (checked before any
- * GPU work), NULL or host pointers, or non-finite / non-positive inputs;
- * ECUDA; ETIMEOUT as for steps_forces.
+ * Errors: EINVAL for n outside [1, STEPS_NOALLOC_MAX_N], NULL or host
+ * pointers, or pointers to another device's memory (all checked before any
+ * GPU work), or non-finite / non-positive inputs (found on the GPU and
+ * reported after the call's one synchronisation; acc_out then holds no
+ * result); ECUDA; ETIMEOUT as for steps_forces.
  * The first call on a device looks up the scratch array's device address and
- * caches it; make that first call before capturing a stream into a graph.
+ * caches it; make that first call before any stream capture begins.
  * Every call shares the scratch array, which keeps the previous call's
  * contents (the call clears what must start at zero): calls that overlap on
  * the GPU -- different streams or host threads on one device -- race and must
@@ -343,14 +345,18 @@ steps_status steps_glass_place(const steps_glass_spec *spec, int64_t n, const do
  * and tile_override are taken from cfgs[0]), t0, a0 and softening (soft[s], or
  * NULL / soft == NULL: Eq. 7 with h_min[s]).  All members share one force
  * launch per step (the far-field grid walks every member's tile pairs) and
- * one CUDA graph per step.
+ * one CUDA graph per step.  Members are padded to multiples of 1,024
+ * particles; unless tile_override names a variant, init times every force
+ * variant of the summation mode whose target block fits that padding on the
+ * members' initial state (median of three evaluations) and keeps the fastest.
  *   n [nsims], pos/vel/mass/soft: arrays of nsims pointers (host or device),
  *   each [n_s][3] or [n_s] in the member's caller order; vel may be NULL.
  * steps_ensemble_run: nsteps KDK steps (Eq. 9-11), dts [nsims][nsteps] host,
  * row-major (member s uses dts[s*nsteps + k] at step k).
  * steps_ensemble_get_state: member s's state in its caller order (any output
  * pointer may be NULL).  steps_ensemble_stats: padded particle total and the
- * near/all tile pairs since the last call.
+ * near/all tile pairs since the last call.  steps_ensemble_variant: index of
+ * the force variant in use (steps_variant_name).
  */
 typedef struct steps_ens steps_ens;
 steps_status steps_ensemble_init(steps_ens **out, int nsims, const int64_t *n,
@@ -361,6 +367,7 @@ steps_status steps_ensemble_init(steps_ens **out, int nsims, const int64_t *n,
 steps_status steps_ensemble_run(steps_ens *e, int nsteps, const double *dts);
 steps_status steps_ensemble_get_state(steps_ens *e, int sim, double *pos, double *vel, double *acc,
                                       double *t, double *a);
+steps_status steps_ensemble_variant(steps_ens *e, int *k);
 steps_status steps_ensemble_stats(steps_ens *e, int64_t *total_particles, uint64_t *near_pairs,
                                   uint64_t *all_pairs);
 void steps_ensemble_free(steps_ens *e);

@@ -312,12 +312,14 @@ steps_status compute_forces(steps_ctx *c) {
     return STEPS_OK;
 }
 
-// Autotuner: for systems of >= 2^17 particles, time one pair-force evaluation
-// with every built variant of the requested summation mode and keep the
-// fastest; the choice is cached per (floor(log2 n), mode) for the process.
+// Autotuner: for systems of >= 2^14 particles, time every built variant of
+// the requested summation mode (one warm-up evaluation, then the median of
+// three timed ones) and keep the fastest; the choice is cached per
+// (floor(log2 n), mode) for the process.  Below 2^14 particles an evaluation
+// is dominated by launch latency and the default is kept.
 steps_status autotune(steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
-    if (c->n < (1 << 17)) return STEPS_OK;
+    if (c->n < (1 << 14)) return STEPS_OK;
     int bucket = 0;
     while ((int64_t(1) << (bucket + 1)) <= c->n) ++bucket;
     const std::pair<int, int> key(bucket, comp ? 1 : 0);
@@ -328,9 +330,9 @@ steps_status autotune(steps_ctx *c) {
     }
     const bool prof = c->profiling;
     c->profiling = false;
-    cudaEvent_t e0, e1;
-    STEPS_CUDA(cudaEventCreate(&e0));
-    STEPS_CUDA(cudaEventCreate(&e1));
+    constexpr int kReps = 3;
+    cudaEvent_t ev[kReps + 1];
+    for (auto &e : ev) STEPS_CUDA(cudaEventCreate(&e));
     int best = c->variant;
     float best_ms = 1e30f;
     steps_status st = STEPS_OK;
@@ -338,18 +340,24 @@ steps_status autotune(steps_ctx *c) {
         if (variant(k).comp != comp) continue;
         st = configure_variant(c, k);
         if (st == STEPS_OK) st = compute_forces(c);  // warm-up (first launch of the variant)
-        if (st == STEPS_OK && cudaEventRecord(e0, c->st) != cudaSuccess) st = STEPS_ECUDA;
-        if (st == STEPS_OK) st = compute_forces(c);
-        if (st == STEPS_OK && cudaEventRecord(e1, c->st) != cudaSuccess) st = STEPS_ECUDA;
+        for (int r = 0; r < kReps && st == STEPS_OK; ++r) {
+            if (cudaEventRecord(ev[r], c->st) != cudaSuccess) st = STEPS_ECUDA;
+            if (st == STEPS_OK) st = compute_forces(c);
+        }
+        if (st == STEPS_OK && cudaEventRecord(ev[kReps], c->st) != cudaSuccess) st = STEPS_ECUDA;
         if (st == STEPS_OK) st = sync_and_check(c);
-        float ms = 0.f;
-        if (st == STEPS_OK && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess && ms < best_ms) {
-            best_ms = ms;
-            best = k;
+        float t[kReps];
+        bool ok = st == STEPS_OK;
+        for (int r = 0; r < kReps && ok; ++r) ok = cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]) == cudaSuccess;
+        if (ok) {
+            std::sort(t, t + kReps);
+            if (t[kReps / 2] < best_ms) {
+                best_ms = t[kReps / 2];
+                best = k;
+            }
         }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    for (auto &e : ev) cudaEventDestroy(e);
     c->profiling = prof;
     STEPS_TRY(st);
     cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st);

@@ -39,12 +39,17 @@ struct steps_ens {
     int dts_cap = 0;
     double *tmp3 = nullptr;    // caller-layout staging of one member
     int64_t tmp3_cap = 0;
-    // FP32 path
+    // FP32 path: staging buffers for every candidate variant, the chosen plan
     Staging stg;
     NearScratch nr;
     SimDesc *dsims = nullptr;
     ForcePlan plan;
     double *partial = nullptr;
+    float4 *fdup_buf = nullptr, *sdup_buf = nullptr;
+    unsigned long long *qmax = nullptr;
+    int *nonfinite = nullptr;
+    int64_t pad = 0;                     // members are padded to multiples of this
+    std::vector<int> candidates;         // variants the autotuner times
     SortScratch srt;
     int *err = nullptr;
     unsigned long long *stats = nullptr;
@@ -54,6 +59,10 @@ struct steps_ens {
 namespace {
 
 constexpr float kAlpha = 0.03125f;
+// Members are padded to a multiple of this many particles: a whole number of
+// target blocks (W x 32 KI) for every variant whose block divides it, so that
+// all of them can run on one layout and the autotuner can compare them.
+constexpr int64_t kEnsPad = 1024;
 
 template <typename T>
 steps_status ens_alloc(steps_ens *e, T **p, size_t count) {
@@ -192,13 +201,44 @@ __global__ void ens_reset_run_kernel(int nsims, double *__restrict__ sc) {
 
 steps_status ens_sync(steps_ens *e) {
     STEPS_CUDA(cudaStreamSynchronize(e->st));
-    int w = 0;
-    STEPS_CUDA(cudaMemcpy(&w, e->err, sizeof(int), cudaMemcpyDeviceToHost));
-    if (w) {
+    int w[3] = {0, 0, 0};  // error word, validation flags, non-finite word
+    STEPS_CUDA(cudaMemcpy(w, e->err, sizeof(w), cudaMemcpyDeviceToHost));
+    if (w[0]) {
         STEPS_CUDA(cudaMemset(e->err, 0, sizeof(int)));
-        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", w);
-        return (steps_status)w;
+        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", w[0]);
+        return (steps_status)w[0];
     }
+    if (w[2]) {
+        STEPS_CUDA(cudaMemset(e->nonfinite, 0, sizeof(int)));
+        set_error("a computed force is NaN or Inf (FP32 overflow of the inputs' scale?)");
+        return STEPS_ENONFINITE;
+    }
+    return STEPS_OK;
+}
+
+// Make variant k the active one: tile size, staging views, the system table
+// and the stream-K plan (buffers were sized for every candidate at init).
+steps_status ens_configure(steps_ens *e, int k) {
+    const Variant &v = variant(k);
+    const int64_t T = 32 * v.KI;
+    e->variant = k;
+    e->stg.T = (int)T;
+    e->stg.ntile = e->NP / T;
+    e->stg.fdup = v.form == 1 ? e->fdup_buf : nullptr;
+    e->stg.sdup = v.form == 2 ? e->sdup_buf : nullptr;
+    e->stg.qmax = e->qmax;
+    std::vector<SimDesc> descs(e->nsims);
+    for (int s = 0; s < e->nsims; ++s) {
+        descs[s] = SimDesc{};
+        descs[s].tile_off = e->off[s] / T;
+        descs[s].ntile = (e->off[s + 1] - e->off[s]) / T;
+    }
+    int64_t bits_words = 0;
+    e->plan = plan_force_multi(k, e->num_sms, descs.data(), e->nsims, e->dsims, &bits_words);
+    e->nr.bits_words = bits_words;
+    e->nr.cap_items = 8 * e->stg.ntile;
+    STEPS_CUDA(cudaMemcpyAsync(e->dsims, descs.data(), sizeof(SimDesc) * e->nsims, cudaMemcpyHostToDevice, e->st));
+    STEPS_CUDA(cudaStreamSynchronize(e->st));
     return STEPS_OK;
 }
 
@@ -223,6 +263,8 @@ steps_status ens_forces(steps_ens *e) {
     STEPS_CUDA(launch_force_f32(e->plan, e->stg, e->partial, e->nr, e->err, e->stats, kAlpha, e->wait_ns,
                                 e->num_sms, e->st));
     STEPS_CUDA(launch_fixup(e->plan, e->stg, e->partial, e->nr, 1.0, e->ax, e->ay, e->az, e->st));
+    // non-finite result check (read at the next synchronising call)
+    STEPS_CUDA(launch_check_finite3(e->NP, e->ax, e->ay, e->az, e->nonfinite, e->st, e->h));
     return STEPS_OK;
 }
 
@@ -262,6 +304,44 @@ steps_status ens_step(steps_ens *e, bool do_sort) {
     return STEPS_OK;
 }
 
+// Autotuner: time one force evaluation of the whole ensemble (a warm-up,
+// then the median of three) with every candidate variant on the members'
+// actual initial state and keep the fastest.
+steps_status ens_autotune(steps_ens *e) {
+    if (e->candidates.size() < 2) return STEPS_OK;
+    constexpr int kReps = 3;
+    cudaEvent_t ev[kReps + 1];
+    for (auto &x : ev) STEPS_CUDA(cudaEventCreate(&x));
+    int best = e->candidates[0];
+    float best_ms = 1e30f;
+    steps_status st = STEPS_OK;
+    for (int k : e->candidates) {
+        if (st != STEPS_OK) break;
+        st = ens_configure(e, k);
+        if (st == STEPS_OK) st = ens_forces(e);  // warm-up
+        for (int r = 0; r < kReps && st == STEPS_OK; ++r) {
+            if (cudaEventRecord(ev[r], e->st) != cudaSuccess) st = STEPS_ECUDA;
+            if (st == STEPS_OK) st = ens_forces(e);
+        }
+        if (st == STEPS_OK && cudaEventRecord(ev[kReps], e->st) != cudaSuccess) st = STEPS_ECUDA;
+        if (st == STEPS_OK) st = ens_sync(e);
+        float t[kReps];
+        bool ok = st == STEPS_OK;
+        for (int r = 0; r < kReps && ok; ++r) ok = cudaEventElapsedTime(&t[r], ev[r], ev[r + 1]) == cudaSuccess;
+        if (ok) {
+            std::sort(t, t + kReps);
+            if (t[kReps / 2] < best_ms) {
+                best_ms = t[kReps / 2];
+                best = k;
+            }
+        }
+    }
+    for (auto &x : ev) cudaEventDestroy(x);
+    STEPS_TRY(st);
+    STEPS_CUDA(cudaMemsetAsync(e->stats, 0, 2 * sizeof(unsigned long long), e->st));
+    return ens_configure(e, best);
+}
+
 void ens_release(steps_ens *e) {
     if (!e) return;
     if (e->st) cudaStreamSynchronize(e->st);
@@ -276,8 +356,33 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
     int dev = 0;
     STEPS_CUDA(cudaGetDevice(&dev));
     STEPS_CUDA(cudaDeviceGetAttribute(&e->num_sms, cudaDevAttrMultiProcessorCount, dev));
-    const Variant &v = variant(e->variant);
-    const int64_t T = 32 * v.KI, BI = (int64_t)v.W * T;
+    // candidates: the requested variant, or every variant of the summation mode
+    // whose target block divides the common padding
+    int64_t BI = kEnsPad;
+    if (e->variant >= 0) {
+        e->candidates.assign(1, e->variant);
+        const Variant &v = variant(e->variant);
+        const int64_t bi = (int64_t)v.W * 32 * v.KI;
+        BI = kEnsPad % bi == 0 ? kEnsPad : bi;
+    } else {
+        const bool comp = cfgs[0].prec != STEPS_F32_NAIVE;
+        for (int k = 0; k < num_variants(); ++k) {
+            const Variant &v = variant(k);
+            if (v.comp == comp && kEnsPad % ((int64_t)v.W * 32 * v.KI) == 0) e->candidates.push_back(k);
+        }
+        if (e->candidates.empty()) {
+            set_error("no force variant fits the ensemble layout");
+            return STEPS_EUNSUPPORTED;
+        }
+    }
+    e->pad = BI;
+    int tmin = 1 << 30;
+    bool any_exp = false, any_sym = false;
+    for (int k : e->candidates) {
+        tmin = std::min(tmin, 32 * variant(k).KI);
+        any_exp |= variant(k).form == 1;
+        any_sym |= variant(k).form == 2;
+    }
     e->off.assign(e->nsims + 1, 0);
     int64_t nmax = 0;
     for (int s = 0; s < e->nsims; ++s) {
@@ -293,41 +398,53 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
     STEPS_TRY(ens_alloc(e, &e->doff, e->nsims + 1));
     STEPS_TRY(ens_alloc(e, &e->sc, (size_t)e->nsims * SC_COUNT));
     STEPS_TRY(ens_alloc(e, &e->cosmo, e->nsims));
-    STEPS_TRY(ens_alloc(e, &e->err, 2));
+    STEPS_TRY(ens_alloc(e, &e->err, 4));
+    e->nonfinite = e->err + 2;
     STEPS_TRY(ens_alloc(e, &e->stats, 2));
     e->tmp3_cap = 3 * nmax;
     STEPS_TRY(ens_alloc(e, &e->tmp3, e->tmp3_cap));
-    STEPS_CUDA(cudaMemsetAsync(e->err, 0, 2 * sizeof(int), e->st));
+    STEPS_CUDA(cudaMemsetAsync(e->err, 0, 4 * sizeof(int), e->st));
     STEPS_CUDA(cudaMemsetAsync(e->stats, 0, 2 * sizeof(unsigned long long), e->st));
-    // staging, tables, near field, sort scratch
-    const int64_t ntile = NP / T;
+    // staging, tables, near field, sort scratch: sized for every candidate
+    const int64_t ntile = NP / tmin;  // most tiles any candidate uses
     STEPS_TRY(ens_alloc(e, &e->stg.jdup, 2 * NP));
     STEPS_TRY(ens_alloc(e, &e->stg.rdup, 2 * NP));
-    if (v.form == 1) STEPS_TRY(ens_alloc(e, &e->stg.fdup, 4 * NP));
+    if (any_exp) STEPS_TRY(ens_alloc(e, &e->fdup_buf, 4 * NP));
+    if (any_sym) {
+        STEPS_TRY(ens_alloc(e, &e->sdup_buf, 2 * NP));
+        STEPS_TRY(ens_alloc(e, &e->nr.sym_acc, 3 * NP));
+        STEPS_TRY(ens_alloc(e, &e->nr.tscale, ntile));
+        STEPS_TRY(ens_alloc(e, &e->nr.tinv, ntile));
+    }
+    STEPS_TRY(ens_alloc(e, &e->qmax, 1));
+    e->nr.nonfinite = e->nonfinite;
     STEPS_TRY(ens_alloc(e, &e->stg.tbox_c, ntile));
     STEPS_TRY(ens_alloc(e, &e->stg.tbox_e, ntile));
     e->stg.n = NP;  // validity comes from h >= 0
     e->stg.np = NP;
-    e->stg.T = (int)T;
-    e->stg.ntile = ntile;
-    std::vector<SimDesc> descs(e->nsims);
-    for (int s = 0; s < e->nsims; ++s) {
-        descs[s] = SimDesc{};
-        descs[s].tile_off = e->off[s] / T;
-        descs[s].ntile = (e->off[s + 1] - e->off[s]) / T;
-    }
     STEPS_TRY(ens_alloc(e, &e->dsims, e->nsims));
-    int64_t bits_words = 0;
-    e->plan = plan_force_multi(e->variant, e->num_sms, descs.data(), e->nsims, e->dsims, &bits_words);
-    STEPS_CUDA(cudaMemcpyAsync(e->dsims, descs.data(), sizeof(SimDesc) * e->nsims, cudaMemcpyHostToDevice, e->st));
-    STEPS_TRY(ens_alloc(e, &e->partial, e->plan.partial_elems));
-    STEPS_TRY(ens_alloc(e, &e->nr.bits, (size_t)bits_words));
-    e->nr.bits_words = bits_words;
+    size_t partial_max = 16;
+    int64_t bits_max = 1;
+    for (int k : e->candidates) {
+        const int64_t T = 32 * variant(k).KI;
+        std::vector<SimDesc> descs(e->nsims);
+        for (int s = 0; s < e->nsims; ++s) {
+            descs[s] = SimDesc{};
+            descs[s].tile_off = e->off[s] / T;
+            descs[s].ntile = (e->off[s + 1] - e->off[s]) / T;
+        }
+        int64_t bw = 0;
+        const ForcePlan pl = plan_force_multi(k, e->num_sms, descs.data(), e->nsims, e->dsims, &bw);
+        partial_max = std::max(partial_max, pl.partial_elems);
+        bits_max = std::max(bits_max, bw);
+    }
+    STEPS_TRY(ens_alloc(e, &e->partial, partial_max));
+    STEPS_TRY(ens_alloc(e, &e->nr.bits, (size_t)bits_max));
     STEPS_TRY(ens_alloc(e, &e->nr.cnt, ntile));
     STEPS_TRY(ens_alloc(e, &e->nr.item_off, ntile + 1));
     STEPS_TRY(ens_alloc(e, &e->nr.meta, 4));
-    e->nr.cap_items = 8 * ntile;
     STEPS_TRY(ens_alloc(e, &e->nr.item_part, (size_t)24 * NP));
+    STEPS_TRY(ens_configure(e, e->candidates[0]));
     int64_t p2 = 2;
     while (p2 < NP) p2 <<= 1;
     e->srt.npow2 = p2;
@@ -406,6 +523,7 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
     STEPS_CUDA(cudaMemcpyAsync(e->cosmo, cs.data(), sizeof(Cosmo) * e->nsims, cudaMemcpyHostToDevice, e->st));
     STEPS_CUDA(cudaMemcpyAsync(e->sc, sc.data(), sizeof(double) * sc.size(), cudaMemcpyHostToDevice, e->st));
     STEPS_TRY(ens_resort(e));
+    STEPS_TRY(ens_autotune(e));
     STEPS_TRY(ens_forces_g(e));
     return ens_sync(e);
 }
@@ -458,13 +576,14 @@ steps_status steps_ensemble_init(steps_ens **out, int nsims, const int64_t *n, c
     e->n.assign(n, n + nsims);
     e->resort_every = cfgs[0].resort_every > 0 ? cfgs[0].resort_every : 8;
     const bool comp = cfgs[0].prec != STEPS_F32_NAIVE;
-    e->variant = -1;
+    e->variant = -1;  // -1: tuned at init among the candidates
     if (cfgs[0].tile_override > 0 && cfgs[0].tile_override <= num_variants()) {
         e->variant = cfgs[0].tile_override - 1;
-    } else {
-        for (int k = 0; k < num_variants() && e->variant < 0; ++k)
-            if (variant(k).comp == comp && variant(k).KI == 4) e->variant = k;
-        if (e->variant < 0) e->variant = 0;
+        if (variant(e->variant).comp != comp) {
+            set_error("tile_override %d does not match the precision mode", cfgs[0].tile_override);
+            delete e;
+            return STEPS_EINVAL;
+        }
     }
     if (cuda_stream) {
         e->st = (cudaStream_t)cuda_stream;
@@ -598,6 +717,15 @@ steps_status steps_ensemble_stats(steps_ens *e, int64_t *total_particles, uint64
     if (total_particles) *total_particles = e->NP;
     if (near_pairs) *near_pairs = h[0];
     if (all_pairs) *all_pairs = h[1];
+    return STEPS_OK;
+}
+
+steps_status steps_ensemble_variant(steps_ens *e, int *k) {
+    if (!e || !k) {
+        set_error("ensemble and k are required");
+        return STEPS_EINVAL;
+    }
+    *k = e->variant;
     return STEPS_OK;
 }
 

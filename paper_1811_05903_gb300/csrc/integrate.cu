@@ -253,12 +253,12 @@ __global__ void finite_kernel(int64_t n, const double *__restrict__ a, int posit
     else if (positive && !(v > 0.0)) atomicOr(flag, 2);
 }
 
-// *flag = 1 if any of a[i], b[i], c[i] (i < n) is NaN or Inf.
+// *flag = 1 if any of a[i], b[i], c[i] (i < n; h[i] >= 0 when h is given) is NaN or Inf.
 __global__ void finite3_kernel(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
-                               const double *__restrict__ c, int *flag) {
+                               const double *__restrict__ c, const double *__restrict__ h, int *flag) {
     bool bad = false;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        bad |= !isfinite(a[i]) || !isfinite(b[i]) || !isfinite(c[i]);
+        if (!h || !(h[i] < 0.0)) bad |= !isfinite(a[i]) || !isfinite(b[i]) || !isfinite(c[i]);
     if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) *flag = 1;
 }
 
@@ -383,9 +383,9 @@ cudaError_t launch_check_finite(int64_t n, const double *a, int positive, int *f
 }
 
 cudaError_t launch_check_finite3(int64_t n, const double *a, const double *b, const double *c, int *flag,
-                                 cudaStream_t st) {
+                                 cudaStream_t st, const double *h) {
     const int64_t blocks = std::min<int64_t>(blocks_for(n, 256), 4 * 152);
-    finite3_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(n, a, b, c, flag);
+    finite3_kernel<<<(unsigned)std::max<int64_t>(blocks, 1), 256, 0, st>>>(n, a, b, c, h, flag);
     return cudaGetLastError();
 }
 

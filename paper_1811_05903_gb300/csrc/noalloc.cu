@@ -96,13 +96,15 @@ steps_status scratch_for_device(unsigned char **out) {
     return STEPS_OK;
 }
 
-bool on_device(const void *p) {
+// Device memory of the current device, or managed memory.
+bool on_device(const void *p, int dev) {
     cudaPointerAttributes at;
     if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+    if (at.type == cudaMemoryTypeManaged) return true;
+    return at.type == cudaMemoryTypeDevice && at.device == dev;
 }
 
 int compensated_small_variant() {
@@ -133,7 +135,9 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
         set_error("h_min must be finite and > 0 when soft is NULL");
         return STEPS_EINVAL;
     }
-    if (!on_device(pos) || !on_device(mass) || !on_device(acc_out) || (soft && !on_device(soft))) {
+    int dev = 0;
+    STEPS_CUDA(cudaGetDevice(&dev));
+    if (!on_device(pos, dev) || !on_device(mass, dev) || !on_device(acc_out, dev) || (soft && !on_device(soft, dev))) {
         set_error("pos, mass, soft and acc_out must be device pointers on the current device");
         return STEPS_EINVAL;
     }
@@ -154,8 +158,6 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
     int *err = reinterpret_cast<int *>(base + L.err);
     int *flag = err + 1;
     int num_sms = 0;
-    int dev = 0;
-    STEPS_CUDA(cudaGetDevice(&dev));
     STEPS_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
 
     // inputs into the scratch SoA (caller order), validated like steps_init
@@ -171,13 +173,7 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
     STEPS_CUDA(launch_check_finite(n, z, 0, flag, st));
     STEPS_CUDA(launch_check_finite(n, m, 1, flag, st));
     STEPS_CUDA(launch_check_finite(n, h, 1, flag, st));
-    int bad = 0;
-    STEPS_CUDA(cudaMemcpyAsync(&bad, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-    STEPS_CUDA(cudaStreamSynchronize(st));
-    if (bad) {
-        set_error("positions must be finite and masses and softening lengths finite and > 0");
-        return STEPS_EINVAL;
-    }
+    // the validation flags are read with the error word at the one synchronisation at the end
     STEPS_CUDA(launch_iota(n, perm, st));
 
     // staging and a stream-K plan whose partial sums fit the fixed scratch
@@ -234,12 +230,17 @@ extern "C" steps_status steps_forces_noalloc(int64_t n, const double *pos, const
                                 0.03125f, 2000000000LL, num_sms, st));
     STEPS_CUDA(launch_fixup(p, s, reinterpret_cast<double *>(base + L.partial), nr, G, ax, ay, az, st));
     STEPS_CUDA(launch_scatter3(n, perm, ax, ay, az, acc_out, st));
-    int e = 0;
-    STEPS_CUDA(cudaMemcpyAsync(&e, err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    int w[2] = {0, 0};  // error word, validation flags
+    STEPS_CUDA(cudaMemcpyAsync(w, err, sizeof(w), cudaMemcpyDeviceToHost, st));
     STEPS_CUDA(cudaStreamSynchronize(st));
-    if (e) {
-        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", e);
-        return (steps_status)e;
+    if (w[1]) {
+        set_error("positions must be finite and masses and softening lengths finite and > 0 "
+                  "(acc_out holds no result)");
+        return STEPS_EINVAL;
+    }
+    if (w[0]) {
+        set_error("a bounded device-side wait ran out (error word %d); the kernel exited early", w[0]);
+        return (steps_status)w[0];
     }
     return STEPS_OK;
 }

@@ -287,9 +287,10 @@ cudaError_t launch_softening(int64_t n, const double *m, double h_min, double *h
 // Input check: *flag |= 1 if a holds NaN/Inf, |= 2 if positive != 0 and some a[i] <= 0.
 cudaError_t launch_check_finite(int64_t n, const double *a, int positive, int *flag,
                                 cudaStream_t st);
-// *flag = 1 if some a[i], b[i] or c[i], i < n, is NaN or Inf (the non-finite result check).
+// *flag = 1 if some a[i], b[i] or c[i], i < n, is NaN or Inf (the non-finite result check);
+// with h given, slots with h[i] < 0 (padding) are skipped.
 cudaError_t launch_check_finite3(int64_t n, const double *a, const double *b, const double *c, int *flag,
-                                 cudaStream_t st);
+                                 cudaStream_t st, const double *h = nullptr);
 cudaError_t launch_set_scalar(double *sc, int slot, double v, cudaStream_t st);
 
 }  // namespace steps

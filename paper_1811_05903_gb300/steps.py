@@ -32,6 +32,7 @@ HEADER_SYMBOLS = [
     "steps_glass_place",
     "steps_force_stats", "steps_get_variant", "steps_forces_noalloc", "steps_set_near_alpha",
     "steps_ensemble_init", "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
+    "steps_ensemble_variant",
     "steps_ensemble_free", "steps_paircount",
     # steps_emu.h
     "steps_emu_create", "steps_emu_set_data", "steps_emu_train", "steps_emu_predict",
@@ -115,6 +116,7 @@ def load(build_if_missing: bool = False):
                                         ctypes.POINTER(steps_config), P]
     lib.steps_ensemble_run.argtypes = [P, I, P]
     lib.steps_ensemble_get_state.argtypes = [P, I, P, P, P, P, P]
+    lib.steps_ensemble_variant.argtypes = [P, ctypes.POINTER(I)]
     lib.steps_ensemble_stats.argtypes = [P, ctypes.POINTER(I64), ctypes.POINTER(ctypes.c_uint64),
                                          ctypes.POINTER(ctypes.c_uint64)]
     lib.steps_paircount.argtypes = [I, P, P, P, D, I, P, P, P]
@@ -139,7 +141,7 @@ def load(build_if_missing: bool = False):
                  "steps_set_memory_limit", "steps_forces_subset", "steps_profile_enable",
                  "steps_profile_read", "steps_profile_read_far", "steps_force_stats", "steps_get_variant",
                  "steps_forces_noalloc", "steps_set_near_alpha", "steps_ensemble_init",
-                 "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats",
+                 "steps_ensemble_run", "steps_ensemble_get_state", "steps_ensemble_stats", "steps_ensemble_variant",
                  "steps_paircount", "steps_emu_create", "steps_emu_set_data", "steps_emu_train",
                  "steps_emu_predict", "steps_emu_gradients", "steps_emu_get_params"]:
         getattr(lib, name).restype = I
@@ -494,6 +496,11 @@ class Ensemble:
         tp, nn, na = ctypes.c_int64(), ctypes.c_uint64(), ctypes.c_uint64()
         _check(load().steps_ensemble_stats(self.ctx, ctypes.byref(tp), ctypes.byref(nn), ctypes.byref(na)))
         return tp.value, nn.value, na.value
+
+    def variant(self) -> int:
+        k = ctypes.c_int()
+        _check(load().steps_ensemble_variant(self.ctx, ctypes.byref(k)))
+        return k.value
 
     def close(self):
         if self.ctx:

@@ -201,3 +201,22 @@ def test_symmetric_bitwise_reproducible():
     finally:
         sim.close()
     assert np.array_equal(a1, a2)
+
+
+@pytest.mark.parametrize("variant", ["default", "sym_ki8_w4"])
+def test_fp32_overflow_is_reported_as_nonfinite(variant):
+    """Finite inputs whose FP32 pair terms overflow (masses near the FP32
+    maximum) make the force evaluation return STEPS_ENONFINITE instead of a
+    silent Inf/NaN; the FP64 path computes the same system finitely."""
+    rng = np.random.default_rng(5)
+    n = 3000
+    pos = rng.normal(size=(n, 3))
+    m = np.full(n, 3.0e38)
+    h = np.full(n, 0.01)
+    p = workloads.Particles(pos=pos, vel=np.zeros_like(pos), mass=m, h_min=0.0)
+    k = 0 if variant == "default" else steps.steps_variants().index(variant) + 1
+    with pytest.raises(steps.StepsError) as e:
+        gpu_forces(p, steps.STEPS_F32_COMP, h=h, tile_override=k)
+    assert e.value.status == steps.STEPS_ENONFINITE, e.value
+    a64 = gpu_forces(p, steps.STEPS_F64, h=h)
+    assert np.isfinite(a64).all()
