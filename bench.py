@@ -41,7 +41,7 @@ L2_FLUSH_BYTES = 512 << 20
 # launch, measured by ncu (one pass, the launch-list run of this bench command)
 # for the named variant at the named size, with the kernel source as committed
 # alongside; any other variant or size reports null.
-FAR_TRAFFIC_BYTES = {}
+FAR_TRAFFIC_BYTES = {("sym_ki8_w4", 1048576): 61_270_000}  # mean of 13 launches, 61.05-61.54 MB
 
 
 def peaks():
@@ -481,7 +481,7 @@ def run_ours(args):
                    "variant": variant_name},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FAR_TRAFFIC_BYTES.get((variant_name, n)),
-                     "kernel": "force_f32_kernel (far field, %s)" % variant_name,
+                     "kernel": "%s (far field, %s)" % ("sym_far_kernel" if variant_name.startswith("sym") else "force_f32_kernel", variant_name),
                      "basis": "%d flop/interaction x N^2 (1 - near tile-pair fraction %.4f) per launch / mean far-field "
                               "launch time (CUDA events on the launching stream, %d launches); peak = %d SMs x 128 FP32 "
                               "lanes x 2 x %.0f MHz (FP32 FMA pipe, no measured FP32 peak on file)"
