@@ -930,6 +930,7 @@ const VariantImpl kVariants[] = {
     STEPS_VARIANT(2, 8, 4, false, 32, 4, 4, false, false, "naive_ki2_w8_u4"),
     // symmetric far field (force_sym.cu): 256-particle tiles, 4 compute warps
     {{8, 4, 4, true, "sym_ki8_w4", 2, 3}, nullptr, near_f32_kernel<8, true, kNearFold>, 0, near_smem_of<8>()},
+    {{4, 4, 4, true, "sym_ki4_w4", 2, 4}, nullptr, near_f32_kernel<4, true, kNearFold>, 0, near_smem_of<4>()},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -938,7 +939,7 @@ constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 int num_variants() { return kNumVariants; }
 const Variant &variant(int k) { return kVariants[k].v; }
 size_t force_smem_bytes(int k) {
-    return kVariants[k].v.form == 2 ? sym_smem_bytes(kVariants[k].v.W) : kVariants[k].smem;
+    return kVariants[k].v.form == 2 ? sym_smem_bytes(kVariants[k].v.KI, kVariants[k].v.W) : kVariants[k].smem;
 }
 
 ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const SimDesc *dev_sims,
@@ -971,7 +972,7 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
     cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
     if (sym) {
         // persistent grid; every unit adds to fixed-point sums, no per-CTA partials
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(W, vi.v.ctas),
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(vi.v.KI, W, vi.v.ctas),
                                                                     units));
         p.grid = (int)grid;
         p.smax = 0;

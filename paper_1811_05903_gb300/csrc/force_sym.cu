@@ -17,7 +17,8 @@
 //    difference of two centres exact in FP32, so a tile pair shares one exact
 //    shift dc = c_I - c_J.
 //  * A unit is (target block b of W tiles, source tile J) with J after the
-//    block; pairs of tiles inside one block go to the near-field kernel.  A
+//    block's first tile; warp w takes target tile b W + w only when it
+//    precedes J, so each pair of distinct tiles is one unit of one warp.  A
 //    persistent grid splits the units evenly (stream-K); source tiles stream
 //    into a shared-memory ring with TMA bulk copies (cp.async.bulk completing
 //    on mbarriers), each stage refilled by the last warp done with it; warp w
@@ -59,11 +60,10 @@ namespace steps {
 
 namespace {
 
-constexpr int kKI = 8;                  // targets per lane
+// KI targets per lane (8: 256-particle tiles, 4: 128-particle tiles) as KI/2
+// packed pairs; kKJ sources per lane and step; a source tile is taken in
+// 32 KI / (32 kKJ) rounds of 32 steps.
 constexpr int kKJ = 2;                  // sources per lane and step
-constexpr int kT = 32 * kKI;            // particles per tile
-constexpr int kR = kT / (32 * kKJ);     // rounds of 32 steps per source tile
-constexpr int kNP = kKI / 2;            // packed target pairs per lane
 constexpr int kFold = 16;               // steps (32 sources) per compensated fold
 
 struct SymArgs {
@@ -83,7 +83,10 @@ struct SymArgs {
 };
 
 // Units of one system in row-major order: row b holds (b, J) for
-// J = (b + 1) W .. ntile - 1.
+// J = b W + 1 .. ntile - 1.  In unit (b, J) warp w takes target tile b W + w
+// only when that tile precedes J, so every pair of distinct tiles belongs to
+// exactly one unit and one warp (the first W - 1 units of a row reach into the
+// block itself).
 template <int W>
 struct UnitCursor {
     int sidx;
@@ -91,29 +94,29 @@ struct UnitCursor {
     int64_t b, J;
 
     __device__ __forceinline__ int64_t row_off(int64_t bb) const {
-        return bb * d.ntile - (int64_t)W * bb * (bb + 1) / 2;
+        return bb * (d.ntile - 1) - (int64_t)W * bb * (bb - 1) / 2;
     }
     __device__ __forceinline__ void locate(const SimDesc *__restrict__ sims, int nsims, int64_t u) {
         sidx = sim_of_unit(sims, nsims, u);
         d = sims[sidx];
         const int64_t v = u - d.unit_off;
-        int64_t lo = 0, hi = d.ntile / W - 1;  // row_off(lo) <= v < row_off(hi)
+        int64_t lo = 0, hi = d.ntile / W;  // row_off(lo) <= v < row_off(hi)
         while (hi - lo > 1) {
             const int64_t mid = (lo + hi) >> 1;
             if (row_off(mid) <= v) lo = mid; else hi = mid;
         }
         b = lo;
-        J = (b + 1) * W + (v - row_off(b));
+        J = b * W + 1 + (v - row_off(b));
     }
     __device__ __forceinline__ void next(const SimDesc *__restrict__ sims, int nsims) {
         if (++J < d.ntile) return;
         ++b;
-        J = (b + 1) * W;
-        while (J >= d.ntile) {  // empty row: the next system with units
+        J = b * W + 1;
+        while (J >= d.ntile) {  // past the last row: the next system with units
             if (++sidx >= nsims) return;
             d = sims[sidx];
             b = 0;
-            J = W;
+            J = 1;
         }
     }
 };
@@ -132,11 +135,13 @@ __device__ __forceinline__ void red_fixed(unsigned long long *addr, float v, flo
 // negated target offsets.  Target sums go to the Kahan state myk; source sums
 // to the fixed-point array (scale scJ) of the source tile starting at
 // particle jbase.
-template <int UNR>
+template <int KI, int UNR>
 __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const float4 meta,
                                              const float2 *__restrict__ myio, float4 *__restrict__ myk,
-                                             const float2 (&mi)[kNP], int lane, int64_t jbase, float scJ,
+                                             const float2 (&mi)[KI / 2], int lane, int64_t jbase, float scJ,
                                              unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
+    constexpr int kNP = KI / 2;
+    constexpr int kR = KI / kKJ;  // rounds of 32 steps (32 KI sources, kKJ per lane and step)
     // The separation is formed as (o_j - o_i) - dc: the offsets are small (tile
     // scale) and dc is exact, so d carries only rounding relative to itself.
     // (Forming a shifted target s = o_i + dc once per unit would save one
@@ -246,16 +251,18 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
 // Fill stage s = k mod NS with unit k of this CTA's range (cursor c): the W
 // warps' metadata (dc, M_J or -1 when that warp's tile pair is near) and the
 // bulk copy of the source tile.  Called by one whole warp.
-template <int W, int NS>
+template <int KI, int W, int NS>
 __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> &c, int64_t k, float4 *sj,
                                           float4 *smeta, uint64_t *full, long long *issued, int lane) {
+    constexpr int kT = 32 * KI;
     constexpr uint32_t BYTES_J = kT * 32u;
     const int s = (int)(k % NS);
     const int64_t jg = c.d.tile_off + c.J;
     if (lane < W) {
         const int64_t il = c.b * W + lane;
         const uint32_t word = a.nearbits[c.d.bits_off + il * c.d.words + (c.J >> 5)];
-        const bool near = (word >> (c.J & 31)) & 1u;
+        // near pairs and target tiles at or after J (their pair with J is another unit's)
+        const bool near = ((word >> (c.J & 31)) & 1u) || il >= c.J;
         const float4 ci = a.tbox_c[c.d.tile_off + il], cj = a.tbox_c[jg];
         // exact: the tile centres lie on a common grid (staging)
         smeta[s * W + lane] = make_float4(__fsub_rn(ci.x, cj.x), __fsub_rn(ci.y, cj.y), __fsub_rn(ci.z, cj.z),
@@ -279,8 +286,10 @@ __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> 
 // NS further on, so every warp of the CTA computes.  (Measured against a
 // dedicated producer warp: the same speed at equal compute warps, and the
 // producer's registers go to a third CTA per SM.)
-template <int W, int NS, int MINB, int UNR>
+template <int KI, int W, int NS, int MINB, int UNR>
 __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) {
+    constexpr int kT = 32 * KI;
+    constexpr int kNP = KI / 2;
     extern __shared__ __align__(128) unsigned char smem[];
     float4 *sj = reinterpret_cast<float4 *>(smem);                          // [NS][2 kT] source tiles
     float4 *smeta = sj + NS * 2 * kT;                                       // [NS][W] (dc, M_J or -1: near)
@@ -314,7 +323,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
     if (warp == 0) {
         UnitCursor<W> p = c;
         for (int64_t k = 0; k < NS && k < count; ++k) {
-            sym_issue<W, NS>(a, p, k, sj, smeta, full, issued, lane);
+            sym_issue<KI, W, NS>(a, p, k, sj, smeta, full, issued, lane);
             p.next(a.sims, a.nsims);
         }
     }
@@ -330,7 +339,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
         __syncwarp();
 #pragma unroll
         for (int q = 0; q < kNP; ++q) {
-            const float4 *p0 = a.sdup + (ig * kKI + 2 * q) * 64 + lane;  // particle 64 q + lane
+            const float4 *p0 = a.sdup + (ig * KI + 2 * q) * 64 + lane;  // particle 64 q + lane
             const float4 *p1 = p0 + 64;                                   // particle 64 q + 32 + lane
             const float4 A0 = p0[0], B0 = p0[32], A1 = p1[0], B1 = p1[32];
             myio[(0 * kNP + q) * 32 + lane] = make_float2(-A0.x, -A1.x);
@@ -357,7 +366,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
             const float4 meta = smeta[s * W + warp];
             if (meta.w >= 0.f) {
                 const int64_t jg = c.d.tile_off + c.J;
-                sym_far_unit<UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT, a.tscale[jg],
+                sym_far_unit<KI, UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT, a.tscale[jg],
                                   a.acc, a.np, a.nonfinite);
             }
             // done with the stage: the last warp refills it with unit k + NS
@@ -371,7 +380,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
             if (__shfl_sync(0xffffffffu, last, 0) && k + NS < count) {
                 UnitCursor<W> p = c;
                 for (int t = 0; t < NS; ++t) p.next(a.sims, a.nsims);
-                sym_issue<W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
+                sym_issue<KI, W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
             }
             c.next(a.sims, a.nsims);
         }
@@ -392,9 +401,8 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
     }
 }
 
-// Near bitmap of every ordered tile pair of a system (pairs inside one target
-// block are near: the far kernel's units start after the block), and the
-// per-tile fixed-point scale.  The scale bounds the tile's far-field sums: a
+// Near bitmap of every ordered tile pair of a system (each tile with itself is
+// near), and the per-tile fixed-point scale.  The scale bounds the tile's far-field sums: a
 // far pair of tiles contributes at most M_J / gap^2 to any particle of I (gap
 // = the distance between their boxes, r >= gap for every pair), so every
 // partial sum of tile I stays below B_I = sum_J M_J / gap_IJ^2; with
@@ -417,7 +425,7 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
         const int64_t J = j0 + lane;
         bool near = false;
         if (J < d.ntile) {
-            if (J / W == I / W) {
+            if (J == I) {
                 near = true;
             } else {
                 const float4 cj = tbox_c[d.tile_off + J], ej = tbox_e[d.tile_off + J];
@@ -449,7 +457,7 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
 }
 
 // acc = G (far field in fixed point + near-field items in item order), sorted order.
-__global__ void sym_fixup_kernel(const unsigned long long *__restrict__ acc, int64_t np,
+__global__ void sym_fixup_kernel(const unsigned long long *__restrict__ acc, int64_t np, int kT,
                                  const double *__restrict__ tinv, const double *__restrict__ item_part,
                                  const int64_t *__restrict__ item_off, int64_t n, double Gc,
                                  double *__restrict__ ax, double *__restrict__ ay, double *__restrict__ az,
@@ -478,32 +486,39 @@ __global__ void sym_fixup_kernel(const unsigned long long *__restrict__ acc, int
 constexpr int kNS = 4;   // stages of the source-tile ring
 constexpr int kUNR = 4;  // steps unrolled
 
-template <int W>
+template <int KI, int W>
 constexpr size_t sym_smem_of() {
-    return (size_t)kNS * 2 * kT * 16 + (size_t)kNS * W * 16 + (size_t)W * 3 * kNP * 32 * 8 +
-           (size_t)W * 3 * kNP * 32 * 16 + kNS * (sizeof(uint64_t) + sizeof(long long) + sizeof(int));
+    return (size_t)kNS * 2 * (32 * KI) * 16 + (size_t)kNS * W * 16 + (size_t)W * 3 * (KI / 2) * 32 * 8 +
+           (size_t)W * 3 * (KI / 2) * 32 * 16 + kNS * (sizeof(uint64_t) + sizeof(long long) + sizeof(int));
 }
 
 using SymFn = void (*)(const SymArgs);
 
-SymFn sym_fn(int W, int ctas) {
-    if (W != 4 || ctas != 3) return nullptr;
-    return sym_far_kernel<4, kNS, 3, kUNR>;
+// The built kernels: 256-particle tiles at 3 CTAs per SM (up to 168
+// registers), 128-particle tiles at 4 CTAs per SM (up to 128).
+SymFn sym_fn(int KI, int W, int ctas) {
+    if (W != 4) return nullptr;
+    if (KI == 8 && ctas == 3) return sym_far_kernel<8, 4, kNS, 3, kUNR>;
+    if (KI == 4 && ctas == 4) return sym_far_kernel<4, 4, kNS, 4, kUNR>;
+    return nullptr;
 }
 
 }  // namespace
 
 int64_t sym_units(int64_t ntile, int W) {
     const int64_t nb = ntile / W;
-    return nb >= 1 ? (nb - 1) * ntile - (int64_t)W * (nb - 1) * nb / 2 : 0;
+    return nb >= 1 ? nb * (ntile - 1) - (int64_t)W * nb * (nb - 1) / 2 : 0;
 }
 
-size_t sym_smem_bytes(int W) { return W == 4 ? sym_smem_of<4>() : 0; }
+size_t sym_smem_bytes(int KI, int W) {
+    if (W != 4) return 0;
+    return KI == 8 ? sym_smem_of<8, 4>() : (KI == 4 ? sym_smem_of<4, 4>() : 0);
+}
 
-int sym_blocks_per_sm(int W, int ctas) {
-    SymFn fn = sym_fn(W, ctas);
+int sym_blocks_per_sm(int KI, int W, int ctas) {
+    SymFn fn = sym_fn(KI, W, ctas);
     if (!fn) return 0;
-    const size_t smem = sym_smem_bytes(W);
+    const size_t smem = sym_smem_bytes(KI, W);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 1;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, fn, W * 32, smem) != cudaSuccess || per < 1)
@@ -523,8 +538,9 @@ cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const Near
 
 cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScratch &nr, int *err,
                            long long wait_ns, cudaStream_t st) {
-    const int W = variant(p.variant).W;
-    SymFn fn = sym_fn(W, variant(p.variant).ctas);
+    const Variant &v = variant(p.variant);
+    const int W = v.W;
+    SymFn fn = sym_fn(v.KI, W, v.ctas);
     if (!fn) return cudaErrorInvalidValue;
     SymArgs a;
     a.sdup = s.sdup;
@@ -541,7 +557,7 @@ cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScrat
     a.units = p.units;
     a.wait_ns = wait_ns;
     if (p.units <= 0) return cudaSuccess;
-    fn<<<p.grid, W * 32, sym_smem_bytes(W), st>>>(a);
+    fn<<<p.grid, W * 32, sym_smem_bytes(v.KI, W), st>>>(a);
     return cudaGetLastError();
 }
 
@@ -550,7 +566,7 @@ cudaError_t launch_sym_fixup(const Staging &s, const ForcePlan &p, const NearScr
     (void)p;
     const int tb = 256;
     const int64_t blocks = (s.n + tb - 1) / tb;
-    sym_fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(nr.sym_acc, s.np, nr.tinv, nr.item_part, nr.item_off, s.n,
+    sym_fixup_kernel<<<(unsigned)blocks, tb, 0, st>>>(nr.sym_acc, s.np, s.T, nr.tinv, nr.item_part, nr.item_off, s.n,
                                                       G, ax, ay, az, nr.nonfinite);
     return cudaGetLastError();
 }

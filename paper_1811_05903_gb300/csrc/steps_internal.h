@@ -49,8 +49,8 @@ struct Variant {
     // particles (explicit separation, 8 lane operations and half an MUFU per
     // interaction; reads Staging::sdup, accumulates in fixed point)
     int form;
-    // symmetric kernel: CTAs of 4 warps per SM it is compiled for (3: up to
-    // 168 registers per thread)
+    // symmetric kernel: CTAs of 4 warps per SM it is compiled for (3 for
+    // 256-particle tiles: up to 168 registers per thread; 4 for 128: up to 128)
     int ctas = 0;
 };
 
@@ -130,14 +130,14 @@ struct ForcePlan {
 ForcePlan plan_force(const Staging &s, int variant, int num_sms);
 
 // Symmetric far field (force_sym.cu).  Units are (target block b of W tiles,
-// source tile J) with J >= (b + 1) W, per system; pairs of tiles inside one
-// block go to the near field.
+// source tile J) with J > b W, per system; warp w of the block takes tile
+// b W + w when it precedes J.
 int64_t sym_units(int64_t ntile, int W);
-size_t sym_smem_bytes(int W);
+size_t sym_smem_bytes(int KI, int W);
 // ctas: the variant's Variant::ctas (which compiled kernel)
-int sym_blocks_per_sm(int W, int ctas);
-// Near bitmap (all ordered tile pairs; same-block pairs are near), per-tile
-// fixed-point scales from a bound on the far-field sums, near/all counts.
+int sym_blocks_per_sm(int KI, int W, int ctas);
+// Near bitmap (all ordered tile pairs; each tile with itself is near),
+// per-tile fixed-point scales from a bound on the far-field sums, near/all counts.
 cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const NearScratch &nr, float alpha,
                                 unsigned long long *stats, cudaStream_t st);
 cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScratch &nr, int *err,

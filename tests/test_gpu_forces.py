@@ -147,22 +147,28 @@ def test_precision_study_full_size_sampled():
     assert np.all(net <= 1e-6 * scale)
 
 
-def sym_variant():
-    """1-based index of the symmetric far-field variant (tile_override)."""
+SYM_VARIANTS = ["sym_ki8_w4", "sym_ki4_w4"]
+
+
+def sym_variant(name="sym_ki8_w4"):
+    """1-based index of a symmetric far-field variant (tile_override)."""
     names = steps.steps_variants()
-    return names.index("sym_ki8_w4") + 1
+    return names.index(name) + 1
 
 
-@pytest.mark.parametrize("n", [1, 2, 255, 256, 257, 1023, 1024, 1025, 4096 + 77, 9000])
-def test_symmetric_small_and_ragged_sizes(n):
+@pytest.mark.parametrize("name", SYM_VARIANTS)
+@pytest.mark.parametrize("n", [1, 2, 127, 128, 255, 256, 257, 1023, 1024, 1025, 4096 + 77, 9000])
+def test_symmetric_small_and_ragged_sizes(n, name):
     """The symmetric far field (each far pair once, applied to both particles):
-    sizes from below one tile to several blocks with a ragged last tile."""
+    sizes from below one tile to several blocks with a ragged last tile, with
+    256- and 128-particle tiles (pairs of tiles inside one target block are
+    far-field work too)."""
     rng = np.random.default_rng(100 + n)
     pos = rng.normal(size=(n, 3)) * np.array([1.0, 2.0, 0.5])
     m = rng.uniform(0.5, 2.0, n)
     h = rng.uniform(0.001, 0.05, n)
     p = workloads.Particles(pos=pos, vel=np.zeros_like(pos), mass=m, h_min=0.0)
-    a = gpu_forces(p, steps.STEPS_F32_COMP, h=h, tile_override=sym_variant())
+    a = gpu_forces(p, steps.STEPS_F32_COMP, h=h, tile_override=sym_variant(name))
     if n == 1:
         assert np.all(a == 0.0)
         return
@@ -171,15 +177,16 @@ def test_symmetric_small_and_ragged_sizes(n):
     assert np.sqrt(np.mean(e ** 2)) <= RMS_TOL and e.max() <= MAX_TOL, (n, np.sqrt(np.mean(e ** 2)), e.max())
 
 
+@pytest.mark.parametrize("name", SYM_VARIANTS)
 @pytest.mark.parametrize("n_central,per_shell", [(16384, 256), (16384 + 301, 128 + 5)])
-def test_symmetric_compactified_and_third_law(n_central, per_shell):
+def test_symmetric_compactified_and_third_law(n_central, per_shell, name):
     """Compactified set (mass ratio ~1e6 between shells and centre): parity with
     the oracle, and the symmetric construction conserves momentum: the far
     field adds +f to one particle and -f to the other in fixed point."""
     p = workloads.compactified(22, n_central, 64, per_shell)
     h = oracle.softening(p.mass, p.h_min)
     ref = oracle.pair_acc(p.pos, p.mass, h, p.G)
-    a = gpu_forces(p, steps.STEPS_F32_COMP, tile_override=sym_variant(), comoving=True)
+    a = gpu_forces(p, steps.STEPS_F32_COMP, tile_override=sym_variant(name), comoving=True)
     e = rel_err(a, ref)
     rms = np.sqrt(np.mean(e ** 2))
     assert rms <= RMS_TOL and e.max() <= MAX_TOL, (rms, e.max())
@@ -203,7 +210,7 @@ def test_symmetric_bitwise_reproducible():
     assert np.array_equal(a1, a2)
 
 
-@pytest.mark.parametrize("variant", ["default", "sym_ki8_w4"])
+@pytest.mark.parametrize("variant", ["default"] + SYM_VARIANTS)
 def test_fp32_overflow_is_reported_as_nonfinite(variant):
     """Finite inputs whose FP32 pair terms overflow (masses near the FP32
     maximum) make the force evaluation return STEPS_ENONFINITE instead of a
