@@ -402,7 +402,9 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
 }
 
 // Near bitmap of every ordered tile pair of a system (each tile with itself is
-// near), and the per-tile fixed-point scale.  The scale bounds the tile's far-field sums: a
+// near; tiles larger than their distance may be far: the separations are
+// exact, and the alpha rule bounds their rounding), and the per-tile
+// fixed-point scale.  The scale bounds the tile's far-field sums: a
 // far pair of tiles contributes at most M_J / gap^2 to any particle of I (gap
 // = the distance between their boxes, r >= gap for every pair), so every
 // partial sum of tile I stays below B_I = sum_J M_J / gap_IJ^2; with
@@ -430,7 +432,7 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
             } else {
                 const float4 cj = tbox_c[d.tile_off + J], ej = tbox_e[d.tile_off + J];
                 float gap2 = 0.f;
-                near = tile_pair_near(ci, ei, cj, ej, alpha2, &gap2);
+                near = tile_pair_near(ci, ei, cj, ej, alpha2, &gap2, false);
                 if (!near) bound += (double)ej.w / (double)gap2;
             }
         }

@@ -191,14 +191,16 @@ __device__ __forceinline__ void near_tile_terms(
 //  * near if some pair may be closer than h_i + h_j (spline branches of Eq. 4);
 //  * near if the boxes are closer than alpha x (|c_I - c_J| + |e_I| + |e_J|),
 //    where one FP32 difference of offsets could lose relative precision in d;
-//  * near if |e_I| + |e_J| > |c_I - c_J|: the far field's first-order
-//    correction of the target shift uses the source tile's monopole tidal
-//    tensor, which needs the tiles to be smaller than their distance.
+//  * near if |e_I| + |e_J| > |c_I - c_J| (extents_rule): the one-sided far
+//    field's first-order correction of the target shift uses the source
+//    tile's monopole tidal tensor, which needs the tiles to be smaller than
+//    their distance.  The symmetric far field forms exact separations and
+//    has no such correction, so it classifies without this rule.
 // gap2_out (may be null) receives the squared distance between the two boxes
 // (rounded down), which bounds r^2 from below for every pair of the tiles.
 __device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei, const float4 cj,
                                                const float4 ej, const float alpha2,
-                                               float *gap2_out = nullptr) {
+                                               float *gap2_out = nullptr, bool extents_rule = true) {
     const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
     const float dcx = __fsub_rn(ci.x, cj.x), dcy = __fsub_rn(ci.y, cj.y), dcz = __fsub_rn(ci.z, cj.z);
     const float gx = fmaxf(0.f, __fsub_rn(__fmul_rn(fabsf(dcx), dn), __fmul_rn(__fadd_rn(ei.x, ej.x), up)));
@@ -213,7 +215,7 @@ __device__ __forceinline__ bool tile_pair_near(const float4 ci, const float4 ei,
     const float nj = __fadd_rn(__fadd_rn(__fmul_rn(ej.x, ej.x), __fmul_rn(ej.y, ej.y)), __fmul_rn(ej.z, ej.z));
     const float dist = __fsqrt_rn(n2);
     const float ext = __fadd_rn(__fsqrt_rn(ni), __fsqrt_rn(nj));
-    if (__fmul_rn(ext, up) > dist) return true;
+    if (extents_rule && __fmul_rn(ext, up) > dist) return true;
     const float scale = __fadd_rn(dist, ext);
     return gap2 < __fmul_rn(alpha2, __fmul_rn(scale, scale));
 }
