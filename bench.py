@@ -255,14 +255,19 @@ def periodic_throughput(steps_mod, n=16384, L=1.0, seed=21):
         steps_mod.steps_forces(sim.ctx)
         steps_mod.steps_profile_read(sim.ctx, reset=True)
         steps_mod.steps_profile_enable(sim.ctx, True)
-        for _ in range(2):
+        for _ in range(3):
             steps_mod.steps_forces(sim.ctx)
+        far_ms, far_launches = steps_mod.steps_profile_read_far(sim.ctx)
         ms, launches, _ = steps_mod.steps_profile_read(sim.ctx, reset=True)
         sim.close()
         per = ms * 1e-3 / max(launches, 1)
+        far = far_ms * 1e-3 / max(far_launches, 1)
         tflops = 20 * terms * n * n / per / 1e12
         out[name] = {"ms_per_evaluation": 1e3 * per, "pair_image_terms_per_s": terms * n * n / per,
-                     "fp32_tflops_at_20_flop": tflops, "frac_of_fp32_peak": tflops / peak}
+                     "fp32_tflops_at_20_flop": tflops, "frac_of_fp32_peak": tflops / peak,
+                     # the image kernel alone: the symmetric kernel (cut sum) or the per-target one
+                     "kernel": "psym_far_kernel" if images == 0 else "periodic_f32_kernel",
+                     "kernel_ms": 1e3 * far, "kernel_share": far / per if per > 0 else None}
     return out
 
 

@@ -92,6 +92,7 @@ struct steps_ctx {
     unsigned long long *qmax = nullptr;   // largest |coordinate| (centre grid of the staging)
     NearScratch nr;                       // near-field bitmap and work items
     double *per_part = nullptr;           // periodic mode: FP64 partials per work item
+    PeriodicSymScratch ps;                // periodic cut sum: symmetric kernel scratch
     SimDesc *dsim = nullptr;              // device table of one system
     unsigned long long *stats = nullptr;  // near / all tile pairs, accumulated
     float alpha = 0.03125f;
@@ -184,13 +185,19 @@ steps_status sync_and_check(steps_ctx *c) {
 // Default variant before tuning (and the choice below 2^17 particles): the
 // first built variant of the requested summation mode with 4 targets per
 // thread; systems below 32,768 particles use 64-particle tiles (2 targets per
-// thread) to limit padding and near-field work.  Periodic mode always stages
-// 64-particle tiles: smaller tiles leave fewer images straddling the cut
-// sphere (measured 3% faster than 128 at 65,536 and 131,072 particles).
+// thread) to limit padding and near-field work.  Periodic mode: the cut image
+// sum runs on the symmetric periodic kernel's 128-particle tiles; the
+// quasi-periodic sum stages 64-particle tiles (fewer images straddle the
+// half-box faces).
 int pick_variant(const steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
     if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())
         return c->cfg.tile_override - 1;
+    if (c->cosmo.periodic && c->cfg.images != 1 && comp) {
+        // the cut image sum: the symmetric periodic kernel's 128-particle tiles
+        for (int k = 0; k < num_variants(); ++k)
+            if (variant(k).form == 2 && 32 * variant(k).KI == periodic_sym_tile()) return k;
+    }
     const int ki = (c->n >= 32768 && !c->cosmo.periodic) ? 4 : 2;
     for (int k = 0; k < num_variants(); ++k) {
         const Variant &v = variant(k);
@@ -213,9 +220,16 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.ntile = c->stg.np / c->stg.T;
     c->stg.jdup = c->jdup_buf;
     c->stg.rdup = c->rdup_buf;
-    c->stg.fdup = (v.form == 1 || c->cosmo.periodic) ? c->fdup_buf : nullptr;
+    // the per-target periodic kernel reads the expansion layout unless the
+    // symmetric periodic kernel takes the far images
+    const bool per_sym = c->cosmo.periodic && c->cfg.images != 1 && v.form == 2 && 32 * v.KI == periodic_sym_tile();
+    c->stg.fdup = (v.form == 1 || (c->cosmo.periodic && !per_sym)) ? c->fdup_buf : nullptr;
     c->stg.sdup = v.form == 2 ? c->sdup_buf : nullptr;
     c->stg.qmax = c->qmax;
+    // periodic mode stages box units with a centre grid of at least 2^-21, so
+    // that every image shift c_I - c_J - n is exact in FP32
+    c->stg.pscale = c->cosmo.periodic ? 1.0 / c->cosmo.box : 1.0;
+    c->stg.qemin = c->cosmo.periodic ? 1 : -1000;
     c->stg.tbox_c = c->tbc_buf;
     c->stg.tbox_e = c->tbe_buf;
     SimDesc d{};
@@ -281,9 +295,12 @@ steps_status compute_forces(steps_ctx *c) {
             launch_stage(c->stg, c->x, c->y, c->z, c->m, c->h, c->st);
             STEPS_CUDA(cudaGetLastError());
             if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
+            const bool sym = c->cfg.images != 1 && c->stg.sdup && c->stg.T == periodic_sym_tile();
             STEPS_CUDA(launch_periodic_f32(c->stg, c->x, c->y, c->z, c->cosmo.box, c->cfg.images, c->cosmo.G,
-                                           c->per_part, c->num_sms, c->ax, c->ay, c->az, c->st));
-            c->kernel_launches += 3;  // stage, periodic, reduce
+                                           c->per_part, sym ? &c->ps : nullptr, c->num_sms, c->ax, c->ay, c->az,
+                                           c->st, f0, f1));
+            // stage, (count, scan, symmetric), per-target, reduce
+            c->kernel_launches += sym ? 6 : 3;
         }
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
     } else if (c->cfg.prec == STEPS_F64) {
@@ -462,8 +479,19 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     // near-field work-item partials: up to 8 items per target tile (the chunk
     // size adapts on the device), 3 doubles per particle per item
     STEPS_TRY(alloc_n(c, &c->nr.item_part, (size_t)24 * c->np));
-    if (c->cosmo.periodic && c->cfg.prec != STEPS_F64)
+    if (c->cosmo.periodic && c->cfg.prec != STEPS_F64) {
         STEPS_TRY(alloc_n(c, &c->per_part, periodic_part_elems(c->np, c->num_sms)));
+        if (c->cfg.images != 1) {
+            const int64_t np_sym = c->np / periodic_sym_tile();
+            const int64_t npairs = periodic_sym_pairs(np_sym);
+            c->ps.acc = c->nr.sym_acc;
+            c->ps.tscale = c->nr.tscale;
+            c->ps.tinv = c->nr.tinv;
+            c->ps.nonfinite = c->nonfinite;
+            STEPS_TRY(alloc_n(c, &c->ps.off, npairs + 2));  // offsets and the work counter
+            STEPS_TRY(alloc_n(c, &c->ps.bnd, npairs));
+        }
+    }
     STEPS_TRY(alloc_n(c, &c->stats, 2));
     STEPS_CUDA(cudaMemsetAsync(c->stats, 0, 2 * sizeof(unsigned long long), c->st));
     STEPS_TRY(alloc_n(c, &c->tbc_buf, c->ntile_cap));

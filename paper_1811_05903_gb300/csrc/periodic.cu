@@ -43,6 +43,7 @@
 #include <algorithm>
 
 #include "pair_terms.cuh"
+#include "periodic_class.cuh"
 #include "steps_internal.h"
 
 namespace steps {
@@ -94,23 +95,6 @@ __device__ __forceinline__ double spline_over_r_d(double r, double H) {
         g = 16.0 / 15.0 + v * (3.2 + v * (6.4 + v * (32.0 / 3.0))) - 1.0 / (15.0 * u * u * u);
     }
     return g * Hinv * Hinv * Hinv;
-}
-
-// The definition's decision in FP64, with the oracle's expression (no contraction).
-__device__ __noinline__ bool include_f64(double xi, double yi, double zi, double xj, double yj, double zj, int nx,
-                                        int ny, int nz, double L, int images) {
-    const double d0x = __dsub_rn(xi, xj), d0y = __dsub_rn(yi, yj), d0z = __dsub_rn(zi, zj);
-    if (images == 1) {
-        return floor(__dadd_rn(__ddiv_rn(d0x, L), 0.5)) == (double)nx &&
-               floor(__dadd_rn(__ddiv_rn(d0y, L), 0.5)) == (double)ny &&
-               floor(__dadd_rn(__ddiv_rn(d0z, L), 0.5)) == (double)nz;
-    }
-    const double dx = __dsub_rn(d0x, __dmul_rn((double)nx, L));
-    const double dy = __dsub_rn(d0y, __dmul_rn((double)ny, L));
-    const double dz = __dsub_rn(d0z, __dmul_rn((double)nz, L));
-    const double r2 = __dadd_rn(__dadd_rn(__dmul_rn(dx, dx), __dmul_rn(dy, dy)), __dmul_rn(dz, dz));
-    const double cut = __dmul_rn(2.6, L);
-    return r2 < __dmul_rn(cut, cut);
 }
 
 // What the per-term FP64 decisions need (sorted FP64 positions and indices).
@@ -530,8 +514,8 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
     const int64_t J0 = ch * a.ntile / a.nchunk, J1 = (ch + 1) * a.ntile / a.nchunk;
     const int g = lane / LPI;           // image slot
     const int ti0 = (lane % LPI) * KF;  // this lane's first target within the tile
-    const float L = (float)a.L;
-    const double cutd = 2.6 * a.L;
+    const float L = (float)a.Ls;  // staging units
+    const double cutd = 2.6 * a.Ls;
     const float cut2 = (float)(cutd * cutd);
     const float halfL = 0.5f * L;
     const int nimg = a.images == 1 ? 27 : 343;
@@ -552,23 +536,27 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
 
     for (int64_t J = J0; J < J1; ++J) {
         __syncwarp();
-        const float4 *src = a.fdup + 4 * J * T;
-        for (int k = lane; k < 4 * T; k += 32) W.sf[k] = src[k];
+        if (!a.residual) {
+            const float4 *src = a.fdup + 4 * J * T;
+            for (int k = lane; k < 4 * T; k += 32) W.sf[k] = src[k];
+        }
         const float4 cj = a.tbox_c[J], ej = a.tbox_e[J];
         if (lane < 21) {
             // c_I - (c_J + nL) in FP64 per axis and n in [-3, 3], split into FP32 value + remainder
             const int ax = lane / 7, nn = lane % 7 - 3;
             const float c0 = ax == 0 ? ci.x : (ax == 1 ? ci.y : ci.z);
             const float c1 = ax == 0 ? cj.x : (ax == 1 ? cj.y : cj.z);
-            const double d = (double)c0 - ((double)c1 + nn * a.L);
+            const double d = (double)c0 - ((double)c1 + nn * a.Ls);
             const float hi = (float)d;
             W.dh[lane] = hi;
             W.dl[lane] = (float)(d - (double)hi);
         }
         __syncwarp();
-        for (int j = lane; j < T; j += 32) {
-            const float kc = W.sf[4 * j + 1].z * cut2;
-            W.sk[j] = make_float4(-kc, -kc, kCutBand * kc, kCutBand * kc);
+        if (!a.residual) {
+            for (int j = lane; j < T; j += 32) {
+                const float kc = W.sf[4 * j + 1].z * cut2;
+                W.sk[j] = make_float4(-kc, -kc, kCutBand * kc, kCutBand * kc);
+            }
         }
         // sort the candidate images of this tile pair into the four lists
         const float wx = __fadd_rn(ei.x, ej.x) * up + mg, wy = __fadd_rn(ei.y, ej.y) * up + mg,
@@ -581,7 +569,14 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
             const int k = k0 + lane;
             int cls = 0;  // 0 none, 1 far inside, 2 far straddling the cut, 3 near, 4 explicit
             bool allin = false;
-            if (k < nimg) {
+            if (k < nimg && a.residual) {
+                // only the images the symmetric kernel leaves out: those that may
+                // hold a softened pair (the same decision, periodic_class.cuh)
+                int nx, ny, nz;
+                periodic_image_of(k, nx, ny, nz);
+                float gap2;
+                if (periodic_image_class(ci, ei, cj, ej, nx, ny, nz, self_tile, &gap2) == kPerSoft) cls = 3;
+            } else if (k < nimg) {
                 int nx, ny, nz;
                 image_of(k, a.images, nx, ny, nz);
                 const float sx = W.dh[nx + 3], sy = W.dh[10 + ny], sz = W.dh[17 + nz];
@@ -635,7 +630,7 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q)
             hx[q] = hy[q] = hz[q] = cx[q] = cy[q] = cz[q] = make_float2(0.f, 0.f);
-        DecideCtx dc{a.x, a.y, a.z, a.n, a.L, a.images, 0, 0, 0, gi0, J * T};
+        DecideCtx dc{a.x, a.y, a.z, a.n, a.L, a.images, 0, 0, 0, gi0, J * T};  // FP64 positions, FP64 box
         for (int b = 0; b < nF; b += IPW) {
             const bool act = b + g < nF;  // idle slots repeat the step's first image and add nothing
             const int k = W.lf[act ? b + g : b];
@@ -713,10 +708,12 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
     }
 }
 
-// Sum each target's work items in item order and apply G (sorted order).
+// Sum each target's work items in item order, add the symmetric kernel's
+// fixed-point sums (acc, or null), and apply G (sorted order).
 __global__ void periodic_reduce_kernel(const double *__restrict__ item_part, int64_t n, int T, int64_t nchunk,
-                                       double G, double *__restrict__ ax, double *__restrict__ ay,
-                                       double *__restrict__ az) {
+                                       const unsigned long long *__restrict__ acc, const double *__restrict__ tinv,
+                                       int64_t np, double G, double *__restrict__ ax, double *__restrict__ ay,
+                                       double *__restrict__ az, int *nonfinite) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n) return;
     const int64_t I = p / T;
@@ -728,9 +725,16 @@ __global__ void periodic_reduce_kernel(const double *__restrict__ item_part, int
         sy += Q[T + li];
         sz += Q[2 * T + li];
     }
+    if (acc) {
+        const double inv = tinv[I];
+        sx += (double)(long long)acc[p] * inv;
+        sy += (double)(long long)acc[np + p] * inv;
+        sz += (double)(long long)acc[2 * np + p] * inv;
+    }
     ax[p] = G * sx;
     ay[p] = G * sy;
     az[p] = G * sz;
+    if (nonfinite && (!isfinite(sx) || !isfinite(sy) || !isfinite(sz))) *nonfinite = 1;
 }
 
 // FP64 comparison path: the definition's loops, one thread per target.
@@ -846,9 +850,20 @@ size_t periodic_part_elems(int64_t np, int num_sms) {
 }
 
 cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                int images, double G, double *item_part, int num_sms, double *ax, double *ay,
-                                double *az, cudaStream_t st) {
-    if (!s.fdup) return cudaErrorInvalidValue;
+                                int images, double G, double *item_part, const PeriodicSymScratch *ps,
+                                int num_sms, double *ax, double *ay, double *az, cudaStream_t st,
+                                cudaEvent_t far_begin, cudaEvent_t far_end) {
+    // the symmetric kernel takes the cut sum's Newtonian images on 128-particle
+    // tiles with its layout; the per-target kernel everything else
+    const bool sym = ps && images != 1 && s.sdup && s.T == periodic_sym_tile();
+    if (!sym && !s.fdup) return cudaErrorInvalidValue;
+    cudaError_t e;
+    if (sym) {
+        if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
+        e = launch_periodic_sym(s, x, y, z, L, *ps, num_sms, st);
+        if (e != cudaSuccess) return e;
+        if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
+    }
     PeriodicArgs a;
     a.jdup = s.jdup;
     a.rdup = s.rdup;
@@ -863,10 +878,12 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
     a.nchunk = periodic_chunks(s.ntile, num_sms);
     a.n = s.n;
     a.L = L;
+    a.Ls = 1.0;  // the staging is in box units
     a.images = images;
+    a.residual = sym ? 1 : 0;
     const int64_t items = a.ntile * a.nchunk;
     const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
-    cudaError_t e;
+    if (!sym && far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
     switch (s.T) {
         case 64: e = launch_tile<64, 4>(a, blocks, st); break;
         case 128: e = launch_tile<128, 4>(a, blocks, st); break;
@@ -874,8 +891,12 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
-    periodic_reduce_kernel<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(item_part, s.n, s.T, a.nchunk, G, ax, ay,
-                                                                         az);
+    if (!sym && far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
+    // forces in box units scale as 1 / L^2
+    const double Gs = G / (L * L);
+    periodic_reduce_kernel<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(
+        item_part, s.n, s.T, a.nchunk, sym ? ps->acc : nullptr, sym ? ps->tinv : nullptr, s.np, Gs, ax, ay, az,
+        ps ? ps->nonfinite : nullptr);
     return cudaGetLastError();
 }
 

@@ -45,11 +45,12 @@ struct SumOp {
 // Largest |coordinate| of the real particles into *out (the bit pattern of a
 // non-negative double orders like the value, so an integer max is exact).
 __global__ void absmax_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                              const double *__restrict__ z, const double *__restrict__ h,
+                              const double *__restrict__ z, const double *__restrict__ h, double pscale,
                               unsigned long long *__restrict__ out) {
     double v = 0.0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        if (!(h[i] < 0.0)) v = fmax(v, fmax(fabs(x[i]), fmax(fabs(y[i]), fabs(z[i]))));
+        if (!(h[i] < 0.0))
+            v = fmax(v, fmax(fabs(x[i] * pscale), fmax(fabs(y[i] * pscale), fabs(z[i] * pscale))));
     for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
     if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(v));
 }
@@ -66,19 +67,19 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              const double *__restrict__ m, const double *__restrict__ h,
                              float4 *__restrict__ jdup, float4 *__restrict__ rdup,
                              float4 *__restrict__ fdup, float4 *__restrict__ sdup,
-                             const unsigned long long *__restrict__ qmax, float4 *__restrict__ tbox_c,
-                             float4 *__restrict__ tbox_e) {
+                             const unsigned long long *__restrict__ qmax, double pscale, int qemin,
+                             float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e) {
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
     const int64_t p = tile * T + threadIdx.x;
     const bool valid = p < n && !(h[p] < 0.0);  // negative softening marks padding
     double px = 0, py = 0, pz = 0, pm = 0, ph = 0;
     if (valid) {
-        px = x[p];
-        py = y[p];
-        pz = z[p];
+        px = x[p] * pscale;
+        py = y[p] * pscale;
+        pz = z[p] * pscale;
         pm = m[p];
-        ph = h[p];
+        ph = h[p] * pscale;
     }
     const double lox = block_reduce(valid ? px : DBL_MAX, sbuf, MinOp());
     const double loy = block_reduce(valid ? py : DBL_MAX, sbuf, MinOp());
@@ -94,10 +95,16 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
     if (qmax) {
         const double amax = __longlong_as_double((long long)*qmax);
         int e = 0;
+        bool grid = false;
         if (amax > 0.0) {
             frexp(amax, &e);  // amax < 2^e
-            q = ldexp(1.0, e - 22);
+            grid = true;
         }
+        if (qemin > -1000 && (!grid || e < qemin)) {
+            e = qemin;
+            grid = true;
+        }
+        if (grid) q = ldexp(1.0, e - 22);
     }
     const float cx = any ? grid_centre(0.5 * (lox + hix), q) : 0.f;
     const float cy = any ? grid_centre(0.5 * (loy + hiy), q) : 0.f;
@@ -300,10 +307,10 @@ void launch_stage(const Staging &s, const double *x, const double *y, const doub
                   const double *m, const double *h, cudaStream_t st) {
     if (s.qmax) {
         cudaMemsetAsync(s.qmax, 0, sizeof(unsigned long long), st);
-        absmax_kernel<<<152, 512, 0, st>>>(s.n, x, y, z, h, s.qmax);
+        absmax_kernel<<<152, 512, 0, st>>>(s.n, x, y, z, h, s.pscale, s.qmax);
     }
-    stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup,
-                                                    s.fdup, s.sdup, s.qmax, s.tbox_c, s.tbox_e);
+    stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup, s.fdup, s.sdup,
+                                                    s.qmax, s.pscale, s.qemin, s.tbox_c, s.tbox_e);
 }
 
 namespace {

@@ -77,6 +77,11 @@ struct Staging {
     // 2^(e-22) with max|x| < 2^e, so that every difference of two centres is
     // exact in FP32.
     unsigned long long *qmax = nullptr;
+    // positions and softenings are multiplied by pscale before staging (1 / L
+    // in periodic mode: box units); with qmax the centre grid is at least
+    // 2^(qemin - 22)
+    double pscale = 1.0;
+    int qemin = -1000;
     float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
 };
@@ -165,25 +170,54 @@ cudaError_t launch_fixup(const ForcePlan &p, const Staging &s, const double *par
                          const NearScratch &nr, double G, double *ax, double *ay, double *az,
                          cudaStream_t st);
 
-// Periodic pair term (Eq. 2 with Eq. 5).  FP32 path on the tile staging
-// (including the far-field expansion layout fdup): work items (target tile,
-// chunk of source tiles) write FP64 partials item_part [ntile * nchunk][3][T]
-// (nchunk = periodic_chunks(ntile, num_sms)), then a reduction applies G into
-// ax, ay, az (sorted order).
+// Periodic pair term (Eq. 2 with Eq. 5).  The staging is in box units
+// (Staging::pscale = 1 / L, tile centres on a grid of 2^-21 or coarser), so
+// every image shift c_I - c_J - n is exact in FP32.
+//
+// Per-target FP32 kernel (periodic.cu): work items (target tile, chunk of
+// source tiles) write FP64 partials item_part [ntile * nchunk][3][T]
+// (nchunk = periodic_chunks(ntile, num_sms)), then a reduction applies G / L^2
+// into ax, ay, az (sorted order).  It takes every image of the quasi-periodic
+// sum and of the cut sum on staging without the symmetric layout; with the
+// symmetric kernel (cut sum, 128-particle tiles) it takes only the images that
+// may hold a softened pair ("residual" mode), and the reduction adds the
+// symmetric kernel's fixed-point sums.
 struct PeriodicArgs {
     const float4 *jdup, *rdup, *fdup, *tbox_c, *tbox_e;
     const double *x, *y, *z;  // FP64 sorted positions: decisions near the cut / half-box faces
     double *item_part;
     int64_t ntile, nchunk, n;
-    double L;
+    double L;   // box length of x, y, z (FP64 decisions)
+    double Ls;  // box length in staging units (1)
     int images;
+    int residual;  // 1: only the images the symmetric kernel leaves out
+};
+// Scratch of the symmetric periodic kernel (periodic_sym.cu).
+struct PeriodicSymScratch {
+    unsigned long long *acc = nullptr;  // [3][np] fixed-point sums
+    float *tscale = nullptr;            // [ntile] 2^(62 - E_t)
+    double *tinv = nullptr;             // [ntile] 2^(E_t - 62)
+    int64_t *off = nullptr;             // [npairs + 2] work-unit offsets of the tile pairs (I <= J), counter
+    float2 *bnd = nullptr;              // [npairs] bound contributions (to I, to J)
+    int *nonfinite = nullptr;
 };
 int64_t periodic_chunks(int64_t ntile, int num_sms);
 // Largest item_part size (doubles) any tile size needs for np padded particles.
 size_t periodic_part_elems(int64_t np, int num_sms);
+// Tile pairs I <= J of ntile tiles, and the tile size the symmetric kernel needs.
+int64_t periodic_sym_pairs(int64_t ntile);
+int periodic_sym_tile();
+// Symmetric kernel alone: fixed-point sums of every non-soft image into ps.acc
+// (box units, without G / L^2), scales into ps.tscale / ps.tinv.
+cudaError_t launch_periodic_sym(const Staging &s, const double *x, const double *y, const double *z, double L,
+                                const PeriodicSymScratch &ps, int num_sms, cudaStream_t st);
+// The whole FP32 periodic evaluation into ax, ay, az.  ps: symmetric scratch,
+// or null for the per-target kernel alone.  far_begin / far_end (optional)
+// bracket the symmetric kernel.
 cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                int images, double G, double *item_part, int num_sms, double *ax, double *ay,
-                                double *az, cudaStream_t st);
+                                int images, double G, double *item_part, const PeriodicSymScratch *ps,
+                                int num_sms, double *ax, double *ay, double *az, cudaStream_t st,
+                                cudaEvent_t far_begin = nullptr, cudaEvent_t far_end = nullptr);
 cudaError_t launch_periodic_f64(int64_t n, const double *x, const double *y, const double *z, const double *m,
                                 const double *h, double G, double L, int images, double *ax, double *ay,
                                 double *az, cudaStream_t st);
