@@ -468,6 +468,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->sdup_buf, 2 * c->np));
     STEPS_TRY(alloc_n(c, &c->qmax, 1));
     STEPS_TRY(alloc_n(c, &c->nr.sym_acc, 3 * c->np));
+    STEPS_TRY(alloc_n(c, &c->nr.sym_next, 1));
     STEPS_TRY(alloc_n(c, &c->nr.tscale, c->ntile_cap));
     STEPS_TRY(alloc_n(c, &c->nr.tinv, c->ntile_cap));
     c->nr.nonfinite = c->nonfinite;

@@ -413,6 +413,7 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
     if (any_sym) {
         STEPS_TRY(ens_alloc(e, &e->sdup_buf, 2 * NP));
         STEPS_TRY(ens_alloc(e, &e->nr.sym_acc, 3 * NP));
+        STEPS_TRY(ens_alloc(e, &e->nr.sym_next, 1));
         STEPS_TRY(ens_alloc(e, &e->nr.tscale, ntile));
         STEPS_TRY(ens_alloc(e, &e->nr.tinv, ntile));
     }

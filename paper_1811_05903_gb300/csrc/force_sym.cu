@@ -79,6 +79,8 @@ struct SymArgs {
     int nsims;
     int64_t np;
     int64_t units;
+    int64_t chunk;              // units per chunk
+    unsigned long long *next;   // chunk counter, zeroed before the launch
     long long wait_ns;
 };
 
@@ -281,11 +283,18 @@ __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> 
 }
 
 // The CTA's W warps share an NS-stage ring of source tiles.  There is no
-// producer warp: warp 0 fills the first NS stages, and afterwards the last
-// warp done with a stage (a shared-memory counter) refills it with the unit
-// NS further on, so every warp of the CTA computes.  (Measured against a
-// dedicated producer warp: the same speed at equal compute warps, and the
+// producer warp: warp 0 fills the first NS stages of a chunk, and afterwards
+// the last warp done with a stage (a shared-memory counter) refills it with
+// the unit NS further on, so every warp of the CTA computes.  (Measured against
+// a dedicated producer warp: the same speed at equal compute warps, and the
 // producer's registers go to a third CTA per SM.)
+//
+// The units are cut into fixed chunks of a.chunk consecutive units, and the
+// persistent CTAs take chunks from a global counter: the warp schedulers favour
+// the CTAs that arrived first on an SM, and with equal static shares the last
+// CTA of each SM ran ~30% longer than the first.  Every chunk starts and
+// flushes its own target sums, so the result does not depend on which CTA
+// takes which chunk.
 template <int KI, int W, int NS, int MINB, int UNR>
 __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) {
     constexpr int kT = 32 * KI;
@@ -297,15 +306,11 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
     float4 *skah = reinterpret_cast<float4 *>(sio + W * 3 * kNP * 32);      // [W][3][kNP][32] Kahan (hi, -c)
     uint64_t *full = reinterpret_cast<uint64_t *>(skah + W * 3 * kNP * 32); // [NS]
     long long *issued = reinterpret_cast<long long *>(full + NS);          // [NS] last unit copied into a stage
-    int *done = reinterpret_cast<int *>(issued + NS);                       // [NS] warps finished with a stage
+    long long *chunk_slot = issued + NS;                                     // [2] the chunk taken, abort flag
+    int *done = reinterpret_cast<int *>(chunk_slot + 2);                    // [NS] warps finished with a stage
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
-    const int64_t G = gridDim.x;
-    const int64_t cta = blockIdx.x;
-    const int64_t u0 = cta * a.units / G;
-    const int64_t u1 = (cta + 1) * a.units / G;
-    const int64_t count = u1 - u0;
 
     if (threadIdx.x == 0) {
         for (int s = 0; s < NS; ++s) {
@@ -313,91 +318,111 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
             issued[s] = -1;
             done[s] = 0;
         }
+        chunk_slot[1] = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
-    if (count <= 0) return;
-
-    UnitCursor<W> c;
-    c.locate(a.sims, a.nsims, u0);
-    if (warp == 0) {
-        UnitCursor<W> p = c;
-        for (int64_t k = 0; k < NS && k < count; ++k) {
-            sym_issue<KI, W, NS>(a, p, k, sj, smeta, full, issued, lane);
-            p.next(a.sims, a.nsims);
-        }
-    }
 
     float2 *myio = sio + warp * 3 * kNP * 32;
     float4 *myk = skah + warp * 3 * kNP * 32;
-    int64_t u = u0;
-    int64_t k = 0;
-    while (u < u1) {
-        const int64_t seg_end = min(u1, c.d.unit_off + c.row_off(c.b + 1));
-        const int64_t ig = c.d.tile_off + c.b * W + warp;  // this warp's target tile
-        float2 mi[kNP];
-        __syncwarp();
-#pragma unroll
-        for (int q = 0; q < kNP; ++q) {
-            const float4 *p0 = a.sdup + (ig * KI + 2 * q) * 64 + lane;  // particle 64 q + lane
-            const float4 *p1 = p0 + 64;                                   // particle 64 q + 32 + lane
-            const float4 A0 = p0[0], B0 = p0[32], A1 = p1[0], B1 = p1[32];
-            myio[(0 * kNP + q) * 32 + lane] = make_float2(-A0.x, -A1.x);
-            myio[(1 * kNP + q) * 32 + lane] = make_float2(-A0.z, -A1.z);
-            myio[(2 * kNP + q) * 32 + lane] = make_float2(-B0.x, -B1.x);
-            mi[q] = make_float2(B0.z, B1.z);
-#pragma unroll
-            for (int cc = 0; cc < 3; ++cc) myk[(cc * kNP + q) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+    int64_t k = 0;  // units this CTA has taken through the ring (stage k mod NS, phase k / NS)
+    for (;;) {
+        if (threadIdx.x == 0) chunk_slot[0] = (long long)atomicAdd(a.next, 1ull);
+        __syncthreads();
+        const int64_t u0 = chunk_slot[0] * a.chunk;
+        const bool abort = chunk_slot[1] != 0;
+        __syncthreads();  // every thread has read the slot before it is written again
+        if (abort || u0 >= a.units) break;
+        const int64_t u1 = min(a.units, u0 + a.chunk);
+        const int64_t count = u1 - u0;
+        const int64_t k0 = k;
+
+        UnitCursor<W> c;
+        c.locate(a.sims, a.nsims, u0);
+        if (warp == 0) {
+            UnitCursor<W> p = c;
+            for (int64_t t = 0; t < NS && t < count; ++t) {
+                sym_issue<KI, W, NS>(a, p, k0 + t, sj, smeta, full, issued, lane);
+                p.next(a.sims, a.nsims);
+            }
         }
-        __syncwarp();
-        for (; u < seg_end; ++u, ++k) {
-            const int s = (int)(k % NS);
-            if (!mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NS) & 1), a.wait_ns)) {
-                if (lane == 0) {
-                    atomicExch(a.err, (int)STEPS_ETIMEOUT);
-                    // drain the copies issued so far before the warp leaves
-                    for (int t = 0; t < NS; ++t) {
-                        const long long q = ((volatile long long *)issued)[t];
-                        if (q >= 0) mbar_wait_bounded(smem_u32(&full[t]), (uint32_t)((q / NS) & 1), kDrainNs);
-                    }
-                }
-                return;
-            }
-            const float4 meta = smeta[s * W + warp];
-            if (meta.w >= 0.f) {
-                const int64_t jg = c.d.tile_off + c.J;
-                sym_far_unit<KI, UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT, a.tscale[jg],
-                                  a.acc, a.np, a.nonfinite);
-            }
-            // done with the stage: the last warp refills it with unit k + NS
+
+        int64_t u = u0;
+        bool failed = false;
+        while (u < u1 && !failed) {
+            const int64_t seg_end = min(u1, c.d.unit_off + c.row_off(c.b + 1));
+            const int64_t ig = c.d.tile_off + c.b * W + warp;  // this warp's target tile
+            float2 mi[kNP];
             __syncwarp();
-            int last = 0;
-            if (lane == 0) {
-                __threadfence_block();
-                last = atomicAdd(&done[s], 1) == W - 1;
-                if (last) done[s] = 0;
-            }
-            if (__shfl_sync(0xffffffffu, last, 0) && k + NS < count) {
-                UnitCursor<W> p = c;
-                for (int t = 0; t < NS; ++t) p.next(a.sims, a.nsims);
-                sym_issue<KI, W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
-            }
-            c.next(a.sims, a.nsims);
-        }
-        // ---- segment done: this warp's target sums into the fixed-point array ----
-        const float scI = a.tscale[ig];
 #pragma unroll
-        for (int q = 0; q < kNP; ++q) {
+            for (int q = 0; q < kNP; ++q) {
+                const float4 *p0 = a.sdup + (ig * KI + 2 * q) * 64 + lane;  // particle 64 q + lane
+                const float4 *p1 = p0 + 64;                                   // particle 64 q + 32 + lane
+                const float4 A0 = p0[0], B0 = p0[32], A1 = p1[0], B1 = p1[32];
+                myio[(0 * kNP + q) * 32 + lane] = make_float2(-A0.x, -A1.x);
+                myio[(1 * kNP + q) * 32 + lane] = make_float2(-A0.z, -A1.z);
+                myio[(2 * kNP + q) * 32 + lane] = make_float2(-B0.x, -B1.x);
+                mi[q] = make_float2(B0.z, B1.z);
 #pragma unroll
-            for (int cc = 0; cc < 3; ++cc) {
-                const float4 K = myk[(cc * kNP + q) * 32 + lane];
-                unsigned long long *dst = a.acc + cc * a.np + ig * kT + 64 * q + lane;
-                red_fixed(dst, K.x, scI, a.nonfinite);
-                red_fixed(dst, K.z, scI, a.nonfinite);
-                red_fixed(dst + 32, K.y, scI, a.nonfinite);
-                red_fixed(dst + 32, K.w, scI, a.nonfinite);
+                for (int cc = 0; cc < 3; ++cc) myk[(cc * kNP + q) * 32 + lane] = make_float4(0.f, 0.f, 0.f, 0.f);
+            }
+            __syncwarp();
+            for (; u < seg_end; ++u, ++k) {
+                const int s = (int)(k % NS);
+                if (!mbar_wait_bounded(smem_u32(&full[s]), (uint32_t)((k / NS) & 1), a.wait_ns)) {
+                    if (lane == 0) {
+                        atomicExch(a.err, (int)STEPS_ETIMEOUT);
+                        // drain the copies issued so far before the CTA leaves
+                        for (int t = 0; t < NS; ++t) {
+                            const long long q = ((volatile long long *)issued)[t];
+                            if (q >= 0) mbar_wait_bounded(smem_u32(&full[t]), (uint32_t)((q / NS) & 1), kDrainNs);
+                        }
+                        ((volatile long long *)chunk_slot)[1] = 1;
+                    }
+                    failed = true;
+                    break;
+                }
+                const float4 meta = smeta[s * W + warp];
+                if (meta.w >= 0.f) {
+                    const int64_t jg = c.d.tile_off + c.J;
+                    sym_far_unit<KI, UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT,
+                                          a.tscale[jg], a.acc, a.np, a.nonfinite);
+                }
+                // done with the stage: the last warp refills it with unit k + NS of the chunk
+                __syncwarp();
+                int last = 0;
+                if (lane == 0) {
+                    __threadfence_block();
+                    last = atomicAdd(&done[s], 1) == W - 1;
+                    if (last) done[s] = 0;
+                }
+                if (__shfl_sync(0xffffffffu, last, 0) && k - k0 + NS < count) {
+                    UnitCursor<W> p = c;
+                    for (int t = 0; t < NS; ++t) p.next(a.sims, a.nsims);
+                    sym_issue<KI, W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
+                }
+                c.next(a.sims, a.nsims);
+            }
+            if (failed) break;
+            // ---- segment done: this warp's target sums into the fixed-point array ----
+            const float scI = a.tscale[ig];
+#pragma unroll
+            for (int q = 0; q < kNP; ++q) {
+#pragma unroll
+                for (int cc = 0; cc < 3; ++cc) {
+                    const float4 K = myk[(cc * kNP + q) * 32 + lane];
+                    unsigned long long *dst = a.acc + cc * a.np + ig * kT + 64 * q + lane;
+                    red_fixed(dst, K.x, scI, a.nonfinite);
+                    red_fixed(dst, K.z, scI, a.nonfinite);
+                    red_fixed(dst + 32, K.y, scI, a.nonfinite);
+                    red_fixed(dst + 32, K.w, scI, a.nonfinite);
+                }
             }
         }
+        // a warp that timed out leaves its ring position behind: every warp
+        // stops at this chunk's end
+        k = k0 + count;
+        __syncthreads();  // every warp is done with every stage before the next chunk's copies
     }
 }
 
@@ -491,7 +516,8 @@ constexpr int kUNR = 4;  // steps unrolled
 template <int KI, int W>
 constexpr size_t sym_smem_of() {
     return (size_t)kNS * 2 * (32 * KI) * 16 + (size_t)kNS * W * 16 + (size_t)W * 3 * (KI / 2) * 32 * 8 +
-           (size_t)W * 3 * (KI / 2) * 32 * 16 + kNS * (sizeof(uint64_t) + sizeof(long long) + sizeof(int));
+           (size_t)W * 3 * (KI / 2) * 32 * 16 + kNS * (sizeof(uint64_t) + sizeof(long long) + sizeof(int)) +
+           2 * sizeof(long long);
 }
 
 using SymFn = void (*)(const SymArgs);
@@ -559,6 +585,13 @@ cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScrat
     a.units = p.units;
     a.wait_ns = wait_ns;
     if (p.units <= 0) return cudaSuccess;
+    if (!nr.sym_next) return cudaErrorInvalidValue;
+    // about 32 chunks per CTA: a finishing tail of ~1/32 of a CTA's share
+    const int64_t want = (int64_t)std::max(p.grid, 1) * 32;
+    a.chunk = std::max<int64_t>(1, (p.units + want - 1) / want);
+    a.next = nr.sym_next;
+    cudaError_t e = cudaMemsetAsync(nr.sym_next, 0, sizeof(unsigned long long), st);
+    if (e != cudaSuccess) return e;
     fn<<<p.grid, W * 32, sym_smem_bytes(v.KI, W), st>>>(a);
     return cudaGetLastError();
 }

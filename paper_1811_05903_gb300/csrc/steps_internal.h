@@ -117,6 +117,7 @@ struct NearScratch {
     float *tscale = nullptr;                // [ntile] 2^(62 - E_t): FP32 value -> fixed point
     double *tinv = nullptr;                 // [ntile] 2^(E_t - 62)
     int *nonfinite = nullptr;               // set to 1 when a far-field partial is not finite
+    unsigned long long *sym_next = nullptr; // chunk counter of the symmetric far kernel
 };
 
 // Stream-K plan for one FP32 force evaluation over one or more systems.

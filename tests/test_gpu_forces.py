@@ -227,3 +227,28 @@ def test_fp32_overflow_is_reported_as_nonfinite(variant):
     assert e.value.status == steps.STEPS_ENONFINITE, e.value
     a64 = gpu_forces(p, steps.STEPS_F64, h=h)
     assert np.isfinite(a64).all()
+
+
+@pytest.mark.parametrize("name", SYM_VARIANTS)
+def test_symmetric_wait_limit_timeout_and_recovery(name):
+    """Every bounded wait of the symmetric kernel's tile ring gives up at once:
+    the evaluation returns STEPS_ETIMEOUT (the CTAs drain their copies and stop
+    at the end of their chunk), and the same context evaluates correctly once
+    the limit is restored."""
+    p = workloads.compactified(62, 16384, 16, 128)
+    cfg = steps.make_config(mode=steps.STEPS_COMOVING, prec=steps.STEPS_F32_COMP, G=p.G, Om=p.Om, OL=p.OL,
+                            tile_override=sym_variant(name))
+    sim = steps.Simulation(p.pos, p.vel, p.mass, h_min=p.h_min, t0=p.t0, a0=p.a0, cfg=cfg)
+    try:
+        steps.steps_set_wait_limit(sim.ctx, 0)
+        with pytest.raises(steps.StepsError) as e:
+            sim.forces()
+        assert e.value.status == steps.STEPS_ETIMEOUT
+        steps.steps_set_wait_limit(sim.ctx, 2_000_000_000)
+        a = sim.forces()
+    finally:
+        sim.close()
+    h = oracle.softening(p.mass, p.h_min)
+    ref = oracle.pair_acc(p.pos, p.mass, h, p.G)
+    e = rel_err(a, ref)
+    assert np.sqrt(np.mean(e ** 2)) <= RMS_TOL and e.max() <= MAX_TOL
