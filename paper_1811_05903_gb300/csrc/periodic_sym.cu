@@ -20,23 +20,24 @@
 // soft (some pair may lie within h_i + h_j, or the n = 0 image of a tile with
 // itself).  This kernel takes the inside and straddling images; the soft ones
 // stay with the per-target kernel (periodic.cu), which classifies with the same
-// function.  A count pass stores the number of images of each tile pair and a
-// bound on each tile's sums; a scan turns the counts into offsets; the far
-// kernel splits the flattened list of (tile pair, image) evenly over
-// persistent warps (stream-K over images).
+// function.  A count pass stores each tile pair's work units (slices of at
+// most kSlice of its images) and a bound on each tile's sums; a scan turns the
+// unit counts into offsets; persistent warps take units from a global counter,
+// so that the warps the schedulers favour take more of them.
 //
 // Inside a warp (as in the open-boundary symmetric kernel): the target tile's
 // 128 particles, 4 per lane as 2 packed pairs; the source tile in shared
 // memory, 2 sources per lane and step, the sources' running sums passed lane to
 // lane by shuffles; two images per pass share o_j - o_i, the loads, the
 // shuffles and the sums; target partials Kahan-folded every 32 sources, source
-// sums Kahan-accumulated over the images of the tile pair.  Straddling images
-// keep a term when r^2 <= (2.6)^2 (1 - 1.5e-6) in FP32 and flag terms within
-// the band (1 +- 1.5e-6) (2.6)^2; a flagged image is rescanned and its band
-// terms decided in FP64 from the FP64 positions with the definition's
-// expression.  All sums
-// go to 64-bit fixed point (red.global.add.u64) with a per-tile power-of-two
-// scale from the count pass's bound: deterministic.
+// sums Kahan-accumulated over the unit's images.  Straddling images keep a term
+// when r^2 <= (2.6)^2 (1 - 1.5e-6) in FP32 and flag terms within the band
+// (1 +- 1.5e-6) (2.6)^2; after each step a warp vote sends the lanes holding
+// flagged terms to recompute that step's terms and decide the band ones in FP64
+// from the FP64 positions with the definition's expression.  All sums go to
+// 64-bit fixed point (red.global.add.u64) with a per-tile power-of-two scale
+// from the count pass's bound; each unit starts and flushes its own sums, so
+// the result does not depend on which warp takes which unit.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
