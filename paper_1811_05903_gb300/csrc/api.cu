@@ -491,6 +491,11 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
             c->ps.nonfinite = c->nonfinite;
             STEPS_TRY(alloc_n(c, &c->ps.off, npairs + 2));  // offsets and the work counter
             STEPS_TRY(alloc_n(c, &c->ps.bnd, npairs));
+            STEPS_TRY(alloc_n(c, &c->ps.soft, npairs));
+            STEPS_TRY(alloc_n(c, &c->ps.soff, np_sym + 1));
+            // the soft partner lists share the item partials of the per-target kernel
+            c->ps.cap_items = (int64_t)(periodic_part_elems(c->np, c->num_sms) / (3 * periodic_sym_tile()));
+            STEPS_TRY(alloc_n(c, &c->ps.slist, c->ps.cap_items));
         }
     }
     STEPS_TRY(alloc_n(c, &c->stats, 2));

@@ -509,9 +509,25 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     WarpSmem<T, KF> &W = reinterpret_cast<WarpSmem<T, KF> *>(periodic_smem)[warp];
     const int64_t item = (int64_t)blockIdx.x * kWarps + warp;
-    if (item >= a.ntile * a.nchunk) return;  // whole warp; warps of a CTA never synchronise
-    const int64_t I = item / a.nchunk, ch = item % a.nchunk;
-    const int64_t J0 = ch * a.ntile / a.nchunk, J1 = (ch + 1) * a.ntile / a.nchunk;
+    int64_t I, J0, J1;
+    if (a.residual && a.soff[a.ntile] <= a.cap_items) {
+        // one source tile that shares a softened image with the target tile
+        if (item >= a.soff[a.ntile]) return;  // whole warp; warps of a CTA never synchronise
+        int64_t lo = 0, hi = a.ntile;         // soff[lo] <= item < soff[hi]
+        while (hi - lo > 1) {
+            const int64_t mid = (lo + hi) >> 1;
+            if (a.soff[mid] <= item) lo = mid; else hi = mid;
+        }
+        I = lo;
+        J0 = a.slist[item];
+        J1 = J0 + 1;
+    } else {
+        if (item >= a.ntile * a.nchunk) return;
+        I = item / a.nchunk;
+        const int64_t ch = item % a.nchunk;
+        J0 = ch * a.ntile / a.nchunk;
+        J1 = (ch + 1) * a.ntile / a.nchunk;
+    }
     const int g = lane / LPI;           // image slot
     const int ti0 = (lane % LPI) * KF;  // this lane's first target within the tile
     const float L = (float)a.Ls;  // staging units
@@ -710,7 +726,8 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
 
 // Sum each target's work items in item order, add the symmetric kernel's
 // fixed-point sums (acc, or null), and apply G (sorted order).
-__global__ void periodic_reduce_kernel(const double *__restrict__ item_part, int64_t n, int T, int64_t nchunk,
+__global__ void periodic_reduce_kernel(const double *__restrict__ item_part, int64_t n, int T, int64_t ntile,
+                                       int64_t nchunk, const int64_t *__restrict__ soff, int64_t cap_items,
                                        const unsigned long long *__restrict__ acc, const double *__restrict__ tinv,
                                        int64_t np, double G, double *__restrict__ ax, double *__restrict__ ay,
                                        double *__restrict__ az, int *nonfinite) {
@@ -719,8 +736,11 @@ __global__ void periodic_reduce_kernel(const double *__restrict__ item_part, int
     const int64_t I = p / T;
     const int li = (int)(p - I * T);
     double sx = 0.0, sy = 0.0, sz = 0.0;
-    for (int64_t ch = 0; ch < nchunk; ++ch) {
-        const double *Q = item_part + (size_t)(I * nchunk + ch) * 3 * T;
+    // the items of target tile I, in item order
+    const bool lists = soff && soff[ntile] <= cap_items;
+    const int64_t it0 = lists ? soff[I] : I * nchunk, it1 = lists ? soff[I + 1] : (I + 1) * nchunk;
+    for (int64_t it = it0; it < it1; ++it) {
+        const double *Q = item_part + (size_t)it * 3 * T;
         sx += Q[li];
         sy += Q[T + li];
         sz += Q[2 * T + li];
@@ -881,7 +901,11 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
     a.Ls = 1.0;  // the staging is in box units
     a.images = images;
     a.residual = sym ? 1 : 0;
-    const int64_t items = a.ntile * a.nchunk;
+    a.soff = sym ? ps->soff : nullptr;
+    a.slist = sym ? ps->slist : nullptr;
+    a.cap_items = sym ? ps->cap_items : 0;
+    // residual mode: enough warps for the soft partner lists or the chunks
+    const int64_t items = sym ? std::max<int64_t>(a.ntile * a.nchunk, ps->cap_items) : a.ntile * a.nchunk;
     const unsigned blocks = (unsigned)((items + kWarps - 1) / kWarps);
     if (!sym && far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
     switch (s.T) {
@@ -895,8 +919,8 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
     // forces in box units scale as 1 / L^2
     const double Gs = G / (L * L);
     periodic_reduce_kernel<<<(unsigned)((s.n + 255) / 256), 256, 0, st>>>(
-        item_part, s.n, s.T, a.nchunk, sym ? ps->acc : nullptr, sym ? ps->tinv : nullptr, s.np, Gs, ax, ay, az,
-        ps ? ps->nonfinite : nullptr);
+        item_part, s.n, s.T, a.ntile, a.nchunk, a.soff, a.cap_items, sym ? ps->acc : nullptr,
+        sym ? ps->tinv : nullptr, s.np, Gs, ax, ay, az, ps ? ps->nonfinite : nullptr);
     return cudaGetLastError();
 }
 

@@ -143,28 +143,37 @@ __device__ __forceinline__ void red_fixed_p(unsigned long long *addr, float v, f
 // at most M / gap^2).
 __global__ void psym_count_kernel(const float4 *__restrict__ tbox_c, const float4 *__restrict__ tbox_e,
                                   int64_t ntile, int64_t npairs, int64_t *__restrict__ uoff,
-                                  float2 *__restrict__ bnd) {
+                                  float2 *__restrict__ bnd, int *__restrict__ soft) {
     const int64_t p = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int lane = threadIdx.x & 31;
     if (p >= npairs) return;
     int64_t I, J;
     pair_of(p, ntile, I, J);
     const float4 ci = tbox_c[I], ei = tbox_e[I], cj = tbox_c[J], ej = tbox_e[J];
-    int cnt = 0;
+    int cnt = 0, nsoft = 0;
     double s = 0.0;
     for (int k0 = 0; k0 < kPerImages; k0 += 32) {
+        const int k = k0 + lane;
         float gap2;
-        const int cls = pair_image_class(ci, ei, cj, ej, I == J, k0 + lane, &gap2);
+        const int cls = pair_image_class(ci, ei, cj, ej, I == J, k, &gap2);
         if (cls == kPerInside || cls == kPerStraddle) {
             ++cnt;
             s += 1.0 / (double)gap2;
         }
+        // images the per-target kernel takes (either half for a tile with itself)
+        if (k < kPerImages) {
+            int nx, ny, nz;
+            periodic_image_of(k, nx, ny, nz);
+            nsoft += periodic_image_class(ci, ei, cj, ej, nx, ny, nz, I == J, &gap2) == kPerSoft ? 1 : 0;
+        }
     }
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+        nsoft += __shfl_xor_sync(0xffffffffu, nsoft, o);
         s += __shfl_xor_sync(0xffffffffu, s, o);
     }
     if (lane == 0) {
+        soft[p] = nsoft;
         uoff[p + 1] = (cnt + kSlice - 1) / kSlice;
         // tile I feels tile J's mass and tile J feels tile I's; a tile with
         // itself feels both halves n and -n (equal gaps)
@@ -172,14 +181,34 @@ __global__ void psym_count_kernel(const float4 *__restrict__ tbox_c, const float
     }
 }
 
+// Inclusive scan of one value per thread over a 1,024-thread CTA.
+__device__ __forceinline__ int64_t block_scan_1024(int64_t v, int64_t *part) {
+    const int t = threadIdx.x;
+    part[t] = v;
+    __syncthreads();
+    for (int d = 1; d < 1024; d <<= 1) {
+        const int64_t w = t >= d ? part[t - d] : 0;
+        __syncthreads();
+        part[t] += w;
+        __syncthreads();
+    }
+    const int64_t r = part[t];
+    __syncthreads();
+    return r;
+}
+
 // One CTA: unit counts -> offsets (uoff[0] = 0, uoff[p + 1] = units of pairs
-// <= p), the work counter zeroed, and each tile's fixed-point scale from the
-// sum of its bounds (in a fixed order): with 2 B < 2^E every partial sum stays
-// below 2^61 at scale 2^(62 - E).
+// <= p), the work counter zeroed, each tile's fixed-point scale from the sum
+// of its bounds (in a fixed order: with 2 B < 2^E every partial sum stays
+// below 2^61 at scale 2^(62 - E)), and for every tile the list of tiles it
+// shares a softened image with, in tile order (soff[I] .. soff[I + 1] into
+// slist, at most cap entries; soff[ntile] is the total even beyond cap).
 __global__ void __launch_bounds__(1024) psym_scan_kernel(int64_t *__restrict__ uoff, int64_t npairs,
                                                          unsigned long long *__restrict__ next,
                                                          const float2 *__restrict__ bnd, int64_t ntile,
-                                                         float *__restrict__ tscale, double *__restrict__ tinv) {
+                                                         float *__restrict__ tscale, double *__restrict__ tinv,
+                                                         const int *__restrict__ soft, int64_t *__restrict__ soff,
+                                                         int *__restrict__ slist, int64_t cap) {
     __shared__ int64_t part[1024];
     const int t = threadIdx.x;
     const int64_t chunk = (npairs + 1023) / 1024;
@@ -215,6 +244,24 @@ __global__ void __launch_bounds__(1024) psym_scan_kernel(int64_t *__restrict__ u
         tscale[I] = ldexpf(1.0f, sh);
         tinv[I] = ldexp(1.0, -sh);
     }
+    // soft partner lists: contiguous tile ranges per thread
+    const int64_t tch = (ntile + 1023) / 1024;
+    const int64_t i0 = t * tch < ntile ? t * tch : ntile, i1 = i0 + tch < ntile ? i0 + tch : ntile;
+    int64_t c = 0;
+    for (int64_t I = i0; I < i1; ++I)
+        for (int64_t J = 0; J < ntile; ++J)
+            c += soft[I <= J ? pair_row_start(I, ntile) + (J - I) : pair_row_start(J, ntile) + (I - J)] > 0;
+    int64_t o = block_scan_1024(c, part) - c;
+    for (int64_t I = i0; I < i1; ++I) {
+        soff[I] = o;
+        for (int64_t J = 0; J < ntile; ++J) {
+            if (soft[I <= J ? pair_row_start(I, ntile) + (J - I) : pair_row_start(J, ntile) + (I - J)] > 0) {
+                if (o < cap) slist[o] = (int)J;
+                ++o;
+            }
+        }
+    }
+    if (t == 1023) soff[ntile] = o;
 }
 
 // The band terms of one step (rare): this lane's terms of the step's kKJ
@@ -584,9 +631,10 @@ cudaError_t launch_periodic_sym(const Staging &s, const double *x, const double 
     cudaError_t e = cudaMemsetAsync(ps.acc, 0, sizeof(unsigned long long) * 3 * s.np, st);
     if (e != cudaSuccess) return e;
     psym_count_kernel<<<(unsigned)((npairs * 32 + 255) / 256), 256, 0, st>>>(s.tbox_c, s.tbox_e, s.ntile, npairs,
-                                                                            ps.off, ps.bnd);
+                                                                            ps.off, ps.bnd, ps.soft);
     unsigned long long *next = reinterpret_cast<unsigned long long *>(ps.off + npairs + 1);
-    psym_scan_kernel<<<1, 1024, 0, st>>>(ps.off, npairs, next, ps.bnd, s.ntile, ps.tscale, ps.tinv);
+    psym_scan_kernel<<<1, 1024, 0, st>>>(ps.off, npairs, next, ps.bnd, s.ntile, ps.tscale, ps.tinv, ps.soft,
+                                         ps.soff, ps.slist, ps.cap_items);
     PSymArgs a;
     a.sdup = s.sdup;
     a.tbox_c = s.tbox_c;

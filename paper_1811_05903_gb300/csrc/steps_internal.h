@@ -192,6 +192,12 @@ struct PeriodicArgs {
     double Ls;  // box length in staging units (1)
     int images;
     int residual;  // 1: only the images the symmetric kernel leaves out
+    // residual mode: items are the entries of the soft partner lists (target
+    // tile by soff, source tile slist[item]) when soff[ntile] <= cap_items,
+    // else (target tile, chunk of source tiles) as in the full mode
+    const int64_t *soff;
+    const int *slist;
+    int64_t cap_items;
 };
 // Scratch of the symmetric periodic kernel (periodic_sym.cu).
 struct PeriodicSymScratch {
@@ -201,6 +207,11 @@ struct PeriodicSymScratch {
     int64_t *off = nullptr;             // [npairs + 2] work-unit offsets of the tile pairs (I <= J), counter
     float2 *bnd = nullptr;              // [npairs] bound contributions (to I, to J)
     int *nonfinite = nullptr;
+    // tiles sharing a softened image (the per-target kernel's work items)
+    int *soft = nullptr;                // [npairs] softened images of the pair
+    int64_t *soff = nullptr;            // [ntile + 1] per target tile, into slist
+    int *slist = nullptr;               // [cap_items] source tiles
+    int64_t cap_items = 0;              // list entries (and item partials) that fit
 };
 int64_t periodic_chunks(int64_t ntile, int num_sms);
 // Largest item_part size (doubles) any tile size needs for np padded particles.
