@@ -185,16 +185,15 @@ steps_status sync_and_check(steps_ctx *c) {
 // Default variant before tuning (and the choice below 2^17 particles): the
 // first built variant of the requested summation mode with 4 targets per
 // thread; systems below 32,768 particles use 64-particle tiles (2 targets per
-// thread) to limit padding and near-field work.  Periodic mode: the cut image
-// sum runs on the symmetric periodic kernel's 128-particle tiles; the
-// quasi-periodic sum stages 64-particle tiles (fewer images straddle the
-// half-box faces).
+// thread) to limit padding and near-field work.  Periodic mode (both the cut
+// image sum and the quasi-periodic sum) runs on the symmetric periodic
+// kernel's 128-particle tiles.
 int pick_variant(const steps_ctx *c) {
     const bool comp = c->cfg.prec != STEPS_F32_NAIVE;
     if (c->cfg.tile_override > 0 && c->cfg.tile_override <= num_variants())
         return c->cfg.tile_override - 1;
-    if (c->cosmo.periodic && c->cfg.images != 1 && comp) {
-        // the cut image sum: the symmetric periodic kernel's 128-particle tiles
+    if (c->cosmo.periodic && comp) {
+        // the symmetric periodic kernel's 128-particle tiles
         for (int k = 0; k < num_variants(); ++k)
             if (variant(k).form == 2 && 32 * variant(k).KI == periodic_sym_tile()) return k;
     }
@@ -222,7 +221,7 @@ steps_status configure_variant(steps_ctx *c, int k) {
     c->stg.rdup = c->rdup_buf;
     // the per-target periodic kernel reads the expansion layout unless the
     // symmetric periodic kernel takes the far images
-    const bool per_sym = c->cosmo.periodic && c->cfg.images != 1 && v.form == 2 && 32 * v.KI == periodic_sym_tile();
+    const bool per_sym = c->cosmo.periodic && v.form == 2 && 32 * v.KI == periodic_sym_tile();
     c->stg.fdup = (v.form == 1 || (c->cosmo.periodic && !per_sym)) ? c->fdup_buf : nullptr;
     c->stg.sdup = v.form == 2 ? c->sdup_buf : nullptr;
     c->stg.qmax = c->qmax;
@@ -295,7 +294,7 @@ steps_status compute_forces(steps_ctx *c) {
             launch_stage(c->stg, c->x, c->y, c->z, c->m, c->h, c->st);
             STEPS_CUDA(cudaGetLastError());
             if (prof) STEPS_CUDA(cudaEventRecord(e0, c->st));
-            const bool sym = c->cfg.images != 1 && c->stg.sdup && c->stg.T == periodic_sym_tile();
+            const bool sym = c->stg.sdup && c->stg.T == periodic_sym_tile();
             STEPS_CUDA(launch_periodic_f32(c->stg, c->x, c->y, c->z, c->cosmo.box, c->cfg.images, c->cosmo.G,
                                            c->per_part, sym ? &c->ps : nullptr, c->num_sms, c->ax, c->ay, c->az,
                                            c->st, f0, f1));
@@ -482,7 +481,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     STEPS_TRY(alloc_n(c, &c->nr.item_part, (size_t)24 * c->np));
     if (c->cosmo.periodic && c->cfg.prec != STEPS_F64) {
         STEPS_TRY(alloc_n(c, &c->per_part, periodic_part_elems(c->np, c->num_sms)));
-        if (c->cfg.images != 1) {
+        {
             const int64_t np_sym = c->np / periodic_sym_tile();
             const int64_t npairs = periodic_sym_pairs(np_sym);
             c->ps.acc = c->nr.sym_acc;

@@ -589,9 +589,11 @@ __global__ void __launch_bounds__(32 * kWarps, 3) periodic_f32_kernel(const Peri
                 // only the images the symmetric kernel leaves out: those that may
                 // hold a softened pair (the same decision, periodic_class.cuh)
                 int nx, ny, nz;
-                periodic_image_of(k, nx, ny, nz);
+                image_of(k, a.images, nx, ny, nz);
                 float gap2;
-                if (periodic_image_class(ci, ei, cj, ej, nx, ny, nz, self_tile, &gap2) == kPerSoft) cls = 3;
+                const int pc = a.images == 1 ? quasi_image_class(ci, ei, cj, ej, nx, ny, nz, self_tile, &gap2)
+                                             : periodic_image_class(ci, ei, cj, ej, nx, ny, nz, self_tile, &gap2);
+                if (pc == kPerSoft) cls = 3;
             } else if (k < nimg) {
                 int nx, ny, nz;
                 image_of(k, a.images, nx, ny, nz);
@@ -873,14 +875,14 @@ cudaError_t launch_periodic_f32(const Staging &s, const double *x, const double 
                                 int images, double G, double *item_part, const PeriodicSymScratch *ps,
                                 int num_sms, double *ax, double *ay, double *az, cudaStream_t st,
                                 cudaEvent_t far_begin, cudaEvent_t far_end) {
-    // the symmetric kernel takes the cut sum's Newtonian images on 128-particle
-    // tiles with its layout; the per-target kernel everything else
-    const bool sym = ps && images != 1 && s.sdup && s.T == periodic_sym_tile();
+    // the symmetric kernel takes the Newtonian images on 128-particle tiles with
+    // its layout; the per-target kernel everything else
+    const bool sym = ps && s.sdup && s.T == periodic_sym_tile();
     if (!sym && !s.fdup) return cudaErrorInvalidValue;
     cudaError_t e;
     if (sym) {
         if (far_begin && (e = cudaEventRecord(far_begin, st)) != cudaSuccess) return e;
-        e = launch_periodic_sym(s, x, y, z, L, *ps, num_sms, st);
+        e = launch_periodic_sym(s, x, y, z, L, images, *ps, num_sms, st);
         if (e != cudaSuccess) return e;
         if (far_end && (e = cudaEventRecord(far_end, st)) != cudaSuccess) return e;
     }

@@ -1,5 +1,6 @@
 // Box tests that sort the images of a tile pair for the periodic pair term
-// (Sec. 2.2, Eq. 5, cut at |x_i - x_j - nL| < 2.6 L), shared by the symmetric
+// (Sec. 2.2, Eq. 5, cut at |x_i - x_j - nL| < 2.6 L, and the quasi-periodic
+// leading term), shared by the symmetric
 // far-field kernel and the per-target kernel so that both make exactly the same
 // decision for every (tile pair, image).
 //
@@ -55,6 +56,46 @@ __device__ __forceinline__ int periodic_image_class(const float4 ci, const float
     const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
     if ((self && nx == 0 && ny == 0 && nz == 0) || gap2 <= __fmul_rn(hs, hs)) return kPerSoft;
     return far2 < __fmul_rn(cut2, dn) ? kPerInside : kPerStraddle;
+}
+
+// Quasi-periodic sum: the single image with x_i - x_j - nL in [-L/2, L/2)^3;
+// candidates |n_c| <= 1 (positions wrapped into the box), index
+// k = 9 (nx + 1) + 3 (ny + 1) + (nz + 1).
+constexpr int kQuasiImages = 27;
+constexpr int kQuasiZeroImage = 13;
+
+__device__ __forceinline__ void quasi_image_of(int k, int &nx, int &ny, int &nz) {
+    nx = k / 9 - 1;
+    ny = (k / 3) % 3 - 1;
+    nz = k % 3 - 1;
+}
+
+// Class of image n of the tile pair (I, J) for the quasi-periodic sum, box
+// units: kPerInside when every pair has |d_c| < 1/2 in every component,
+// kPerStraddle when some may, kPerNone when none can, kPerSoft as above.  The
+// same margins as the cut sum's tests; symmetric under the exchange.
+__device__ __forceinline__ int quasi_image_class(const float4 ci, const float4 ei, const float4 cj, const float4 ej,
+                                                 int nx, int ny, int nz, bool self, float *gap2_out) {
+    const float up = 1.0f + 0x1p-18f, dn = 1.0f - 0x1p-18f;
+    const float mg = 1e-5f;
+    const float sx = __fsub_rn(__fsub_rn(ci.x, cj.x), (float)nx);
+    const float sy = __fsub_rn(__fsub_rn(ci.y, cj.y), (float)ny);
+    const float sz = __fsub_rn(__fsub_rn(ci.z, cj.z), (float)nz);
+    const float wx = __fadd_rn(__fmul_rn(__fadd_rn(ei.x, ej.x), up), mg);
+    const float wy = __fadd_rn(__fmul_rn(__fadd_rn(ei.y, ej.y), up), mg);
+    const float wz = __fadd_rn(__fmul_rn(__fadd_rn(ei.z, ej.z), up), mg);
+    const float ax = fabsf(sx), ay = fabsf(sy), az = fabsf(sz);
+    const float gx = fmaxf(0.f, __fsub_rn(ax, wx)), gy = fmaxf(0.f, __fsub_rn(ay, wy)),
+                gz = fmaxf(0.f, __fsub_rn(az, wz));
+    const float gap2 = __fmaf_rn(gz, gz, __fmaf_rn(gy, gy, __fmul_rn(gx, gx)));
+    *gap2_out = gap2;
+    const float half_up = __fmul_rn(0.5f, up), half_dn = __fmul_rn(0.5f, dn);
+    if (!(gx < half_up && gy < half_up && gz < half_up)) return kPerNone;
+    const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
+    if ((self && nx == 0 && ny == 0 && nz == 0) || gap2 <= __fmul_rn(hs, hs)) return kPerSoft;
+    return (__fadd_rn(ax, wx) < half_dn && __fadd_rn(ay, wy) < half_dn && __fadd_rn(az, wz) < half_dn)
+               ? kPerInside
+               : kPerStraddle;
 }
 
 namespace {

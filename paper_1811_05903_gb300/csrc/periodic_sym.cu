@@ -68,6 +68,9 @@ constexpr float kCut2 = 2.6f * 2.6f;
 // from FP64 (|o| <= 1/2 box), o_j - o_i and (o_j - o_i) - D rounded once each
 // (D exact), three roundings in r^2; the band leaves a factor 3.4.
 constexpr float kBandRel = 1.5e-6f;
+// Quasi-periodic sum: band around the half-box faces, max_c |d_c| within
+// 2e-6 of 1/2 (box units; the FP32 separation is within ~1e-7 of exact).
+constexpr float kQuasiBand = 2e-6f;
 constexpr uint16_t kStraddle = 0x8000;
 
 struct PSymWarp {
@@ -119,14 +122,29 @@ __device__ __forceinline__ void pair_of(int64_t p, int64_t ntile, int64_t &I, in
     J = lo + (p - pair_row_start(lo, ntile));
 }
 
+// Candidate images of a tile pair: the cut sum's 343 or the quasi-periodic 27.
+template <bool QUASI>
+__device__ __forceinline__ void image_vec(int k, int &nx, int &ny, int &nz) {
+    if (QUASI) quasi_image_of(k, nx, ny, nz); else periodic_image_of(k, nx, ny, nz);
+}
+
+template <bool QUASI>
+__device__ __forceinline__ int image_class(const float4 ci, const float4 ei, const float4 cj, const float4 ej, int k,
+                                           bool self, float *gap2) {
+    int nx, ny, nz;
+    image_vec<QUASI>(k, nx, ny, nz);
+    return QUASI ? quasi_image_class(ci, ei, cj, ej, nx, ny, nz, self, gap2)
+                 : periodic_image_class(ci, ei, cj, ej, nx, ny, nz, self, gap2);
+}
+
 // Whether image k of the tile pair (I, J), I <= J, is this kernel's work.
+template <bool QUASI>
 __device__ __forceinline__ int pair_image_class(const float4 ci, const float4 ei, const float4 cj, const float4 ej,
                                                 bool self, int k, float *gap2) {
     *gap2 = 0.f;
-    if (k >= kPerImages || (self && k <= kPerZeroImage)) return kPerNone;
-    int nx, ny, nz;
-    periodic_image_of(k, nx, ny, nz);
-    return periodic_image_class(ci, ei, cj, ej, nx, ny, nz, self, gap2);
+    const int nimg = QUASI ? kQuasiImages : kPerImages, zero = QUASI ? kQuasiZeroImage : kPerZeroImage;
+    if (k >= nimg || (self && k <= zero)) return kPerNone;
+    return image_class<QUASI>(ci, ei, cj, ej, k, self, gap2);
 }
 
 __device__ __forceinline__ void red_fixed_p(unsigned long long *addr, float v, float sc, int *nonfinite) {
@@ -141,6 +159,7 @@ __device__ __forceinline__ void red_fixed_p(unsigned long long *addr, float v, f
 // images this kernel evaluates), and the bound sum over those images of
 // M / gap^2 for each side (gap: distance between the boxes, so every term is
 // at most M / gap^2).
+template <bool QUASI>
 __global__ void psym_count_kernel(const float4 *__restrict__ tbox_c, const float4 *__restrict__ tbox_e,
                                   int64_t ntile, int64_t npairs, int64_t *__restrict__ uoff,
                                   float2 *__restrict__ bnd, int *__restrict__ soft) {
@@ -152,20 +171,17 @@ __global__ void psym_count_kernel(const float4 *__restrict__ tbox_c, const float
     const float4 ci = tbox_c[I], ei = tbox_e[I], cj = tbox_c[J], ej = tbox_e[J];
     int cnt = 0, nsoft = 0;
     double s = 0.0;
-    for (int k0 = 0; k0 < kPerImages; k0 += 32) {
+    const int nimg = QUASI ? kQuasiImages : kPerImages;
+    for (int k0 = 0; k0 < nimg; k0 += 32) {
         const int k = k0 + lane;
         float gap2;
-        const int cls = pair_image_class(ci, ei, cj, ej, I == J, k, &gap2);
+        const int cls = pair_image_class<QUASI>(ci, ei, cj, ej, I == J, k, &gap2);
         if (cls == kPerInside || cls == kPerStraddle) {
             ++cnt;
             s += 1.0 / (double)gap2;
         }
         // images the per-target kernel takes (either half for a tile with itself)
-        if (k < kPerImages) {
-            int nx, ny, nz;
-            periodic_image_of(k, nx, ny, nz);
-            nsoft += periodic_image_class(ci, ei, cj, ej, nx, ny, nz, I == J, &gap2) == kPerSoft ? 1 : 0;
-        }
+        if (k < nimg) nsoft += image_class<QUASI>(ci, ei, cj, ej, k, I == J, &gap2) == kPerSoft ? 1 : 0;
     }
     for (int o = 16; o > 0; o >>= 1) {
         cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
@@ -267,12 +283,15 @@ __global__ void __launch_bounds__(1024) psym_scan_kernel(int64_t *__restrict__ u
 // The band terms of one step (rare): this lane's terms of the step's kKJ
 // sources are recomputed with the main loop's FP32 operations, and those in
 // the band are decided in FP64 from the FP64 positions with the definition's
-// expression and added to both sides.
-template <int M>
+// expression.  The cut sum's decision is the same for both particles; the
+// quasi-periodic one is taken for each side (the half-open interval makes the
+// image of (j, i) differ from -n exactly on a face), and each side gets its
+// term only when its own decision keeps it.
+template <int M, bool QUASI>
 __device__ __noinline__ void psym_band_step(const BandCtx &bc, PSymWarp &Wm, const float2 (&mi)[kNP],
                                             const float (&D)[M][3], const int (&nn)[M][3], int r, int st,
                                             int lane) {
-    const float band = kBandRel * kCut2;
+    const float band = QUASI ? kQuasiBand : kBandRel * kCut2;
     const int g = (lane + st) & 31;
     for (int k = 0; k < kKJ; ++k) {
         const float4 A = Wm.sj[(r * kKJ + k) * 64 + g], B = Wm.sj[(r * kKJ + k) * 64 + 32 + g];
@@ -291,29 +310,35 @@ __device__ __noinline__ void psym_band_step(const BandCtx &bc, PSymWarp &Wm, con
                 float r2 = __fmul_rn(dx, dx);
                 r2 = __fmaf_rn(dy, dy, r2);
                 r2 = __fmaf_rn(dz, dz, r2);
-                const float u = __fadd_rn(r2, -kCut2);
+                const float u = QUASI ? __fadd_rn(fmaxf(fabsf(dx), fmaxf(fabsf(dy), fabsf(dz))), -0.5f)
+                                      : __fadd_rn(r2, -kCut2);
                 if (!(fabsf(u) < band)) continue;
-                if (gj == gi || gi >= bc.n || gj >= bc.n ||
-                    !include_f64(bc.x[gi], bc.y[gi], bc.z[gi], bc.x[gj], bc.y[gj], bc.z[gj], nn[im][0], nn[im][1],
-                                 nn[im][2], bc.L, 0))
-                    continue;
+                if (gj == gi || gi >= bc.n || gj >= bc.n) continue;
+                const bool in_t = include_f64(bc.x[gi], bc.y[gi], bc.z[gi], bc.x[gj], bc.y[gj], bc.z[gj], nn[im][0],
+                                              nn[im][1], nn[im][2], bc.L, QUASI ? 1 : 0);
+                const bool in_s = QUASI ? include_f64(bc.x[gj], bc.y[gj], bc.z[gj], bc.x[gi], bc.y[gi], bc.z[gi],
+                                                      -nn[im][0], -nn[im][1], -nn[im][2], bc.L, 1)
+                                        : in_t;
+                if (!in_t && !in_s) continue;
                 const float w = rsqrt_approx(r2);
                 const float u3 = w * w * w;
                 const float d3[3] = {dx, dy, dz};
                 const float m_i = e ? mi[q].y : mi[q].x;
 #pragma unroll
                 for (int c = 0; c < 3; ++c) {
-                    float4 &K = Wm.myk[(c * kNP + q) * 32 + lane];
-                    float hi = e ? K.y : K.x, nc = e ? K.w : K.z;
-                    kahan1(hi, nc, u3 * B.z * d3[c]);
-                    if (e) {
-                        K.y = hi;
-                        K.w = nc;
-                    } else {
-                        K.x = hi;
-                        K.z = nc;
+                    if (in_t) {
+                        float4 &K = Wm.myk[(c * kNP + q) * 32 + lane];
+                        float hi = e ? K.y : K.x, nc = e ? K.w : K.z;
+                        kahan1(hi, nc, u3 * B.z * d3[c]);
+                        if (e) {
+                            K.y = hi;
+                            K.w = nc;
+                        } else {
+                            K.x = hi;
+                            K.z = nc;
+                        }
                     }
-                    red_fixed_p(bc.acc + c * bc.np + gj, -(u3 * m_i * d3[c]), bc.scJ, bc.nonfinite);
+                    if (in_s) red_fixed_p(bc.acc + c * bc.np + gj, -(u3 * m_i * d3[c]), bc.scJ, bc.nonfinite);
                 }
             }
         }
@@ -330,7 +355,7 @@ __device__ __noinline__ void psym_band_step(const BandCtx &bc, PSymWarp &Wm, con
 // psym_band_step.  DIAG: a tile with itself; a particle meets its own image at
 // step 0 of round r (target 2 r + k against source k of the step), and that
 // pair is left out.
-template <int M, bool CUT, bool DIAG>
+template <int M, bool CUT, bool DIAG, bool QUASI>
 __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP], const float (&D)[M][3],
                                             const int (&nn)[M][3], const BandCtx &bc, const int lane) {
     float2 ndx[M], ndy[M], ndz[M];
@@ -341,7 +366,8 @@ __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP
         ndz[im] = make_float2(-D[im][2], -D[im][2]);
     }
     const float2 ncut = make_float2(-kCut2, -kCut2);
-    const float band = kBandRel * kCut2;
+    const float band = QUASI ? kQuasiBand : kBandRel * kCut2;
+    const float2 nhalf = make_float2(-0.5f, -0.5f);
     float2 nox[kNP], noy[kNP], noz[kNP];
     float2 px[kNP], py[kNP], pz[kNP];
 #pragma unroll
@@ -388,7 +414,12 @@ __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP
                                 if (k == 0) w.x = 0.f; else w.y = 0.f;
                             }
                             if (CUT) {
-                                const float2 u = __fadd2_rn(r2, ncut);  // r^2 - (2.6)^2
+                                // r^2 - (2.6)^2, or max_c |d_c| - 1/2 (quasi-periodic)
+                                const float2 u =
+                                    QUASI ? __fadd2_rn(make_float2(fmaxf(fabsf(dx.x), fmaxf(fabsf(dy.x), fabsf(dz.x))),
+                                                                   fmaxf(fabsf(dx.y), fmaxf(fabsf(dy.y), fabsf(dz.y)))),
+                                                       nhalf)
+                                          : __fadd2_rn(r2, ncut);
                                 amb = amb | (fabsf(u.x) < band) | (fabsf(u.y) < band);
                                 w.x = u.x <= -band ? w.x : 0.f;
                                 w.y = u.y <= -band ? w.y : 0.f;
@@ -424,7 +455,7 @@ __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP
                     Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
                 }
                 if (CUT && __any_sync(0xffffffffu, amb)) {
-                    if (amb) psym_band_step<M>(bc, Wm, mi, D, nn, r, st, lane);
+                    if (amb) psym_band_step<M, QUASI>(bc, Wm, mi, D, nn, r, st, lane);
                     __syncwarp();
                 }
             }
@@ -459,22 +490,23 @@ __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP
     }
 }
 
-template <int M>
+template <int M, bool QUASI>
 __device__ __forceinline__ void psym_pass(PSymWarp &Wm, const float2 (&mi)[kNP], const float (&D)[M][3],
                                           const int (&nn)[M][3], const BandCtx &bc, bool cut, bool self,
                                           int lane) {
     if (cut) {
-        if (self) psym_images<M, true, true>(Wm, mi, D, nn, bc, lane);
-        else psym_images<M, true, false>(Wm, mi, D, nn, bc, lane);
+        if (self) psym_images<M, true, true, QUASI>(Wm, mi, D, nn, bc, lane);
+        else psym_images<M, true, false, QUASI>(Wm, mi, D, nn, bc, lane);
     } else {
-        if (self) psym_images<M, false, true>(Wm, mi, D, nn, bc, lane);
-        else psym_images<M, false, false>(Wm, mi, D, nn, bc, lane);
+        if (self) psym_images<M, false, true, QUASI>(Wm, mi, D, nn, bc, lane);
+        else psym_images<M, false, false, QUASI>(Wm, mi, D, nn, bc, lane);
     }
 }
 
 // Persistent warps take work units (a tile pair and a slice of its images)
 // from a global counter, so that warps the scheduler favours take more units
 // and all finish together.
+template <bool QUASI>
 __global__ void __launch_bounds__(kWarpsS * 32, kMinBlocks) psym_far_kernel(const PSymArgs a) {
     extern __shared__ __align__(16) unsigned char psym_smem[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -547,9 +579,9 @@ __global__ void __launch_bounds__(kWarpsS * 32, kMinBlocks) psym_far_kernel(cons
         int cnt = 0;
         for (int pass = 0; pass < 2; ++pass) {  // images wholly inside the cut sphere, then straddling ones
             const int want = pass == 0 ? kPerInside : kPerStraddle;
-            for (int k0 = 0; k0 < kPerImages; k0 += 32) {
+            for (int k0 = 0; k0 < (QUASI ? kQuasiImages : kPerImages); k0 += 32) {
                 float gap2;
-                const bool keep = pair_image_class(ci, ei, cj, ej, self, k0 + lane, &gap2) == want;
+                const bool keep = pair_image_class<QUASI>(ci, ei, cj, ej, self, k0 + lane, &gap2) == want;
                 const unsigned bk = __ballot_sync(0xffffffffu, keep);
                 if (keep)
                     Wm.lst[cnt + __popc(bk & ((1u << lane) - 1u))] = (uint16_t)((k0 + lane) | (pass ? kStraddle : 0));
@@ -571,7 +603,7 @@ __global__ void __launch_bounds__(kWarpsS * 32, kMinBlocks) psym_far_kernel(cons
             bool cut = false;
             for (int im = 0; im < M; ++im) {
                 const int code = Wm.lst[l + im];
-                periodic_image_of(code & 0x1ff, nn[im][0], nn[im][1], nn[im][2]);
+                image_vec<QUASI>(code & 0x1ff, nn[im][0], nn[im][1], nn[im][2]);
                 // exact: grid centres, integer n
                 D[im][0] = __fsub_rn(dcx, (float)nn[im][0]);
                 D[im][1] = __fsub_rn(dcy, (float)nn[im][1]);
@@ -579,11 +611,11 @@ __global__ void __launch_bounds__(kWarpsS * 32, kMinBlocks) psym_far_kernel(cons
                 cut = cut || (code & kStraddle);
             }
             if (M == 2) {
-                psym_pass<2>(Wm, mi, D, nn, bc, cut, self, lane);
+                psym_pass<2, QUASI>(Wm, mi, D, nn, bc, cut, self, lane);
             } else {
                 const float D1[1][3] = {{D[0][0], D[0][1], D[0][2]}};
                 const int n1[1][3] = {{nn[0][0], nn[0][1], nn[0][2]}};
-                psym_pass<1>(Wm, mi, D1, n1, bc, cut, self, lane);
+                psym_pass<1, QUASI>(Wm, mi, D1, n1, bc, cut, self, lane);
             }
             l += M;
         }
@@ -605,13 +637,15 @@ __global__ void __launch_bounds__(kWarpsS * 32, kMinBlocks) psym_far_kernel(cons
     }
 }
 
+template <bool QUASI>
 int psym_blocks_per_sm() {
     static int cached = 0;
     if (cached > 0) return cached;
     const size_t smem = sizeof(PSymWarp) * kWarpsS;
-    cudaFuncSetAttribute(psym_far_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaFuncSetAttribute(psym_far_kernel<QUASI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     int per = 1;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, psym_far_kernel, kWarpsS * 32, smem) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, psym_far_kernel<QUASI>, kWarpsS * 32, smem) !=
+            cudaSuccess ||
         per < 1)
         per = 1;
     cached = per;
@@ -625,13 +659,17 @@ int64_t periodic_sym_pairs(int64_t ntile) { return ntile * (ntile + 1) / 2; }
 int periodic_sym_tile() { return kT; }
 
 cudaError_t launch_periodic_sym(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                const PeriodicSymScratch &ps, int num_sms, cudaStream_t st) {
+                                int images, const PeriodicSymScratch &ps, int num_sms, cudaStream_t st) {
+    const bool quasi = images == 1;
     if (s.T != kT || !s.sdup) return cudaErrorInvalidValue;
     const int64_t npairs = periodic_sym_pairs(s.ntile);
     cudaError_t e = cudaMemsetAsync(ps.acc, 0, sizeof(unsigned long long) * 3 * s.np, st);
     if (e != cudaSuccess) return e;
-    psym_count_kernel<<<(unsigned)((npairs * 32 + 255) / 256), 256, 0, st>>>(s.tbox_c, s.tbox_e, s.ntile, npairs,
-                                                                            ps.off, ps.bnd, ps.soft);
+    const unsigned cblocks = (unsigned)((npairs * 32 + 255) / 256);
+    if (quasi)
+        psym_count_kernel<true><<<cblocks, 256, 0, st>>>(s.tbox_c, s.tbox_e, s.ntile, npairs, ps.off, ps.bnd, ps.soft);
+    else
+        psym_count_kernel<false><<<cblocks, 256, 0, st>>>(s.tbox_c, s.tbox_e, s.ntile, npairs, ps.off, ps.bnd, ps.soft);
     unsigned long long *next = reinterpret_cast<unsigned long long *>(ps.off + npairs + 1);
     psym_scan_kernel<<<1, 1024, 0, st>>>(ps.off, npairs, next, ps.bnd, s.ntile, ps.tscale, ps.tinv, ps.soft,
                                          ps.soff, ps.slist, ps.cap_items);
@@ -653,8 +691,10 @@ cudaError_t launch_periodic_sym(const Staging &s, const double *x, const double 
     a.n = s.n;
     a.L = L;
     const size_t smem = sizeof(PSymWarp) * kWarpsS;
-    const int grid = std::max(num_sms, 1) * psym_blocks_per_sm();
-    psym_far_kernel<<<grid, kWarpsS * 32, smem, st>>>(a);
+    if (quasi)
+        psym_far_kernel<true><<<std::max(num_sms, 1) * psym_blocks_per_sm<true>(), kWarpsS * 32, smem, st>>>(a);
+    else
+        psym_far_kernel<false><<<std::max(num_sms, 1) * psym_blocks_per_sm<false>(), kWarpsS * 32, smem, st>>>(a);
     return cudaGetLastError();
 }
 

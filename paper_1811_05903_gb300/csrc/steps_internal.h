@@ -219,10 +219,11 @@ size_t periodic_part_elems(int64_t np, int num_sms);
 // Tile pairs I <= J of ntile tiles, and the tile size the symmetric kernel needs.
 int64_t periodic_sym_pairs(int64_t ntile);
 int periodic_sym_tile();
-// Symmetric kernel alone: fixed-point sums of every non-soft image into ps.acc
-// (box units, without G / L^2), scales into ps.tscale / ps.tinv.
+// Symmetric kernel alone: fixed-point sums of every non-soft image of the cut
+// sum (images 0) or the quasi-periodic sum (images 1) into ps.acc (box units,
+// without G / L^2), scales into ps.tscale / ps.tinv.
 cudaError_t launch_periodic_sym(const Staging &s, const double *x, const double *y, const double *z, double L,
-                                const PeriodicSymScratch &ps, int num_sms, cudaStream_t st);
+                                int images, const PeriodicSymScratch &ps, int num_sms, cudaStream_t st);
 // The whole FP32 periodic evaluation into ax, ay, az.  ps: symmetric scratch,
 // or null for the per-target kernel alone.  far_begin / far_end (optional)
 // bracket the symmetric kernel.

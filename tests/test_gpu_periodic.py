@@ -134,15 +134,16 @@ def test_periodic_small_and_ragged(images, n):
         assert e.max() <= (1e-12 if prec == steps.STEPS_F64 else MAX_TOL), (prec, e.max())
 
 
+@pytest.mark.parametrize("images", [0, 1])
 @pytest.mark.parametrize("n", [127, 128, 129, 511, 513, 2000])
-def test_periodic_symmetric_ragged_tiles(n):
-    """The cut image sum's default path (the symmetric kernel on 128-particle
+def test_periodic_symmetric_ragged_tiles(n, images):
+    """The default path of both sums (the symmetric kernel on 128-particle
     tiles, padding to 512): sizes around one tile and one padded block, every
     target against the oracle."""
     L = 1.0
-    pos, m, h = clumpy_box(300 + n, n, L)
-    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, 0)
-    sim = periodic_sim(pos, m, h, L, 0, steps.STEPS_F32_COMP)
+    pos, m, h = clumpy_box(300 + n + images, n, L)
+    ref = oracle.pair_acc_periodic(pos, m, h, 1.0, L, images)
+    sim = periodic_sim(pos, m, h, L, images, steps.STEPS_F32_COMP)
     got = sim.forces()
     sim.close()
     e = rel_err(got, ref)
@@ -150,15 +151,17 @@ def test_periodic_symmetric_ragged_tiles(n):
     assert rms <= RMS_TOL and e.max() <= MAX_TOL, (n, rms, e.max())
 
 
-def test_periodic_symmetric_third_law_bitwise_and_per_target_kernel():
+@pytest.mark.parametrize("images", [0, 1])
+def test_periodic_symmetric_third_law_bitwise_and_per_target_kernel(images):
     """Each Newtonian (tile pair, image) is evaluated once and added to both
-    particles in 64-bit fixed point: the net force vanishes to rounding, two
-    evaluations agree bit for bit, and the per-target kernel on the same
-    128-particle tiles (each order of every pair evaluated separately) agrees
-    within the FP32 contract."""
+    particles in 64-bit fixed point: the net force vanishes to rounding (no
+    pair of these random positions sits exactly on a half-box face, where the
+    quasi-periodic sum is not antisymmetric), two evaluations agree bit for
+    bit, and the per-target kernel on the same 128-particle tiles (each order
+    of every pair evaluated separately) agrees within the FP32 contract."""
     L, n = 2.0, 4000
-    pos, m, h = clumpy_box(77, n, L)
-    sim = periodic_sim(pos, m, h, L, 0, steps.STEPS_F32_COMP)
+    pos, m, h = clumpy_box(77 + images, n, L)
+    sim = periodic_sim(pos, m, h, L, images, steps.STEPS_F32_COMP)
     a1 = sim.forces()
     a2 = sim.forces()
     sim.close()
@@ -166,7 +169,7 @@ def test_periodic_symmetric_third_law_bitwise_and_per_target_kernel():
     net = np.abs((m[:, None] * a1).sum(0))
     scale = (m[:, None] * np.abs(a1)).sum()
     assert np.all(net <= 1e-6 * scale), net / scale
-    sim = periodic_sim(pos, m, h, L, 0, steps.STEPS_F32_COMP, variant="comp_ki4_w4_u4")
+    sim = periodic_sim(pos, m, h, L, images, steps.STEPS_F32_COMP, variant="comp_ki4_w4_u4")
     b = sim.forces()
     sim.close()
     e = rel_err(a1, b)
