@@ -298,8 +298,8 @@ steps_status compute_forces(steps_ctx *c) {
             STEPS_CUDA(launch_periodic_f32(c->stg, c->x, c->y, c->z, c->cosmo.box, c->cfg.images, c->cosmo.G,
                                            c->per_part, sym ? &c->ps : nullptr, c->num_sms, c->ax, c->ay, c->az,
                                            c->st, f0, f1));
-            // stage, (count, scan, symmetric), per-target, reduce
-            c->kernel_launches += sym ? 6 : 3;
+            // absmax, stage, (count, scan, symmetric), per-target, reduce
+            c->kernel_launches += sym ? 7 : 4;
         }
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
     } else if (c->cfg.prec == STEPS_F64) {
@@ -317,7 +317,8 @@ steps_status compute_forces(steps_ctx *c) {
         if (prof) STEPS_CUDA(cudaEventRecord(e1, c->st));
         STEPS_CUDA(launch_fixup(c->plan, c->stg, c->partial, c->nr, c->cosmo.G, c->ax, c->ay,
                                 c->az, c->st));
-        c->kernel_launches += 6;  // stage, far, near count, near scan, near, fixup
+        // absmax, stage, (classify,) far, near count, near scan, near, fixup
+        c->kernel_launches += variant(c->variant).form == 2 ? 8 : 7;
     }
     // non-finite result check (read at the next synchronising call: STEPS_ENONFINITE)
     STEPS_CUDA(launch_check_finite3(c->n, c->ax, c->ay, c->az, c->nonfinite, c->st));
