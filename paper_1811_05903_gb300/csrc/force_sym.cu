@@ -163,7 +163,12 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
     const int from = (lane + 1) & 31;
 #pragma unroll 1
     for (int r = 0; r < kR; ++r) {
-        float2 Sx[kKJ], Sy[kKJ], Sz[kKJ];  // running sums of the sources of group (lane + step) mod 32
+        // running sums of the sources of group (lane + step) mod 32: with 4 targets
+        // per lane the two packed halves are added before the rotation (6
+        // shuffles per step instead of 12; measured 2% faster there, 1% slower
+        // with 8 targets per lane)
+        constexpr bool kOne = KI == 4;
+        float2 Sx[kKJ], Sy[kKJ], Sz[kKJ];
 #pragma unroll
         for (int k = 0; k < kKJ; ++k) Sx[k] = Sy[k] = Sz[k] = make_float2(0.f, 0.f);
 #pragma unroll 1
@@ -206,19 +211,27 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
                             tz = __ffma2_rn(sj, dz, tz);
                         }
                     }
-                    Sx[k] = __fadd2_rn(Sx[k], tx);
-                    Sy[k] = __fadd2_rn(Sy[k], ty);
-                    Sz[k] = __fadd2_rn(Sz[k], tz);
+                    if constexpr (kOne) {
+                        Sx[k].x = __fadd_rn(Sx[k].x, __fadd_rn(tx.x, tx.y));
+                        Sy[k].x = __fadd_rn(Sy[k].x, __fadd_rn(ty.x, ty.y));
+                        Sz[k].x = __fadd_rn(Sz[k].x, __fadd_rn(tz.x, tz.y));
+                    } else {
+                        Sx[k] = __fadd2_rn(Sx[k], tx);
+                        Sy[k] = __fadd2_rn(Sy[k], ty);
+                        Sz[k] = __fadd2_rn(Sz[k], tz);
+                    }
                 }
                 // pass the group's sums on: lane l takes over group (l + st + 1) mod 32
 #pragma unroll
                 for (int k = 0; k < kKJ; ++k) {
                     Sx[k].x = __shfl_sync(0xffffffffu, Sx[k].x, from);
-                    Sx[k].y = __shfl_sync(0xffffffffu, Sx[k].y, from);
                     Sy[k].x = __shfl_sync(0xffffffffu, Sy[k].x, from);
-                    Sy[k].y = __shfl_sync(0xffffffffu, Sy[k].y, from);
                     Sz[k].x = __shfl_sync(0xffffffffu, Sz[k].x, from);
-                    Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
+                    if constexpr (!kOne) {
+                        Sx[k].y = __shfl_sync(0xffffffffu, Sx[k].y, from);
+                        Sy[k].y = __shfl_sync(0xffffffffu, Sy[k].y, from);
+                        Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
+                    }
                 }
             }
             // fold the target partials into the compensated sums
