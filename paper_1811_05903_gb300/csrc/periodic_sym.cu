@@ -28,7 +28,8 @@
 // Inside a warp (as in the open-boundary symmetric kernel): the target tile's
 // 128 particles, 4 per lane as 2 packed pairs; the source tile in shared
 // memory, 2 sources per lane and step, the sources' running sums passed lane to
-// lane by shuffles; two images per pass share o_j - o_i, the loads, the
+// lane by shuffles (the two packed target halves added first: one shuffle per
+// component); two images per pass share o_j - o_i, the loads, the
 // shuffles and the sums; target partials Kahan-folded every 32 sources, source
 // sums Kahan-accumulated over the unit's images.  Straddling images keep a term
 // when r^2 <= (2.6)^2 (1 - 1.5e-6) in FP32 and flag terms within the band
@@ -441,18 +442,16 @@ __device__ __forceinline__ void psym_images(PSymWarp &Wm, const float2 (&mi)[kNP
                             }
                         }
                     }
-                    Sx[k] = __fadd2_rn(Sx[k], tx);
-                    Sy[k] = __fadd2_rn(Sy[k], ty);
-                    Sz[k] = __fadd2_rn(Sz[k], tz);
+                    // the two packed target halves are added before the rotation
+                    Sx[k].x = __fadd_rn(Sx[k].x, __fadd_rn(tx.x, tx.y));
+                    Sy[k].x = __fadd_rn(Sy[k].x, __fadd_rn(ty.x, ty.y));
+                    Sz[k].x = __fadd_rn(Sz[k].x, __fadd_rn(tz.x, tz.y));
                 }
 #pragma unroll
                 for (int k = 0; k < kKJ; ++k) {
                     Sx[k].x = __shfl_sync(0xffffffffu, Sx[k].x, from);
-                    Sx[k].y = __shfl_sync(0xffffffffu, Sx[k].y, from);
                     Sy[k].x = __shfl_sync(0xffffffffu, Sy[k].x, from);
-                    Sy[k].y = __shfl_sync(0xffffffffu, Sy[k].y, from);
                     Sz[k].x = __shfl_sync(0xffffffffu, Sz[k].x, from);
-                    Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
                 }
                 if (CUT && __any_sync(0xffffffffu, amb)) {
                     if (amb) psym_band_step<M, QUASI>(bc, Wm, mi, D, nn, r, st, lane);
