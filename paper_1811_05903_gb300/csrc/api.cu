@@ -89,6 +89,9 @@ struct steps_ctx {
     Staging stg;
     float4 *jdup_buf = nullptr, *rdup_buf = nullptr, *fdup_buf = nullptr, *tbc_buf = nullptr, *tbe_buf = nullptr;
     float4 *sdup_buf = nullptr;           // symmetric-kernel layout
+    float4 *hbc_buf = nullptr, *hbe_buf = nullptr;  // half-tile boxes (256-particle symmetric variant)
+    uint8_t *submask_buf = nullptr;       // its sub-block near masks
+    int64_t submask_cap = 0;
     unsigned long long *qmax = nullptr;   // largest |coordinate| (centre grid of the staging)
     NearScratch nr;                       // near-field bitmap and work items
     double *per_part = nullptr;           // periodic mode: FP64 partials per work item
@@ -235,6 +238,24 @@ steps_status configure_variant(steps_ctx *c, int k) {
     d.tile_off = 0;
     d.ntile = c->stg.ntile;
     c->plan = plan_force_multi(k, c->num_sms, &d, 1, c->dsim, &c->nr.bits_words);
+    // the 256-particle symmetric variant classifies 128 x 128 sub-blocks
+    const bool sub = v.form == 2 && v.sub;
+    if (sub) {
+        if (!c->hbc_buf) {
+            STEPS_TRY(alloc_n(c, &c->hbc_buf, 2 * (c->np / 256) + 2));
+            STEPS_TRY(alloc_n(c, &c->hbe_buf, 2 * (c->np / 256) + 2));
+        }
+        if (c->plan.mask_bytes > c->submask_cap) {
+            dev_free(c, c->submask_buf);
+            c->submask_buf = nullptr;
+            c->submask_cap = 0;
+            STEPS_TRY(alloc_n(c, &c->submask_buf, (size_t)c->plan.mask_bytes));
+            c->submask_cap = c->plan.mask_bytes;
+        }
+    }
+    c->stg.tbox_hc = sub ? c->hbc_buf : nullptr;
+    c->stg.tbox_he = sub ? c->hbe_buf : nullptr;
+    c->nr.submask = sub ? c->submask_buf : nullptr;
     STEPS_CUDA(cudaMemcpyAsync(c->dsim, &d, sizeof(d), cudaMemcpyHostToDevice, c->st));
     STEPS_CUDA(cudaStreamSynchronize(c->st));
     c->nr.cap_items = 8 * (c->np / c->stg.T);

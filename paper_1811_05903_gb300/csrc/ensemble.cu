@@ -46,6 +46,8 @@ struct steps_ens {
     ForcePlan plan;
     double *partial = nullptr;
     float4 *fdup_buf = nullptr, *sdup_buf = nullptr;
+    float4 *hbox_c = nullptr, *hbox_e = nullptr;  // half-tile boxes (256-particle symmetric variant)
+    uint8_t *submask = nullptr;                   // its sub-block near masks
     unsigned long long *qmax = nullptr;
     int *nonfinite = nullptr;
     int64_t pad = 0;                     // members are padded to multiples of this
@@ -226,6 +228,10 @@ steps_status ens_configure(steps_ens *e, int k) {
     e->stg.ntile = e->NP / T;
     e->stg.fdup = v.form == 1 ? e->fdup_buf : nullptr;
     e->stg.sdup = v.form == 2 ? e->sdup_buf : nullptr;
+    const bool sub = v.form == 2 && v.sub;
+    e->stg.tbox_hc = sub ? e->hbox_c : nullptr;
+    e->stg.tbox_he = sub ? e->hbox_e : nullptr;
+    e->nr.submask = sub ? e->submask : nullptr;
     e->stg.qmax = e->qmax;
     std::vector<SimDesc> descs(e->nsims);
     for (int s = 0; s < e->nsims; ++s) {
@@ -416,6 +422,15 @@ steps_status ens_init_impl(steps_ens *e, const double *const *pos, const double 
         STEPS_TRY(ens_alloc(e, &e->nr.sym_next, 1));
         STEPS_TRY(ens_alloc(e, &e->nr.tscale, ntile));
         STEPS_TRY(ens_alloc(e, &e->nr.tinv, ntile));
+        // sub-blocks of 256-particle tiles: half boxes and a mask per tile pair of a member
+        int64_t mbytes = 0;
+        for (int s = 0; s < e->nsims; ++s) {
+            const int64_t nt = (e->off[s + 1] - e->off[s]) / 256;
+            mbytes += nt * ((nt + 31) / 32) * 32;  // a byte per bit of the member's near bitmap
+        }
+        STEPS_TRY(ens_alloc(e, &e->hbox_c, 2 * (NP / 256) + 2));
+        STEPS_TRY(ens_alloc(e, &e->hbox_e, 2 * (NP / 256) + 2));
+        STEPS_TRY(ens_alloc(e, &e->submask, mbytes + 16));
     }
     STEPS_TRY(ens_alloc(e, &e->qmax, 1));
     e->nr.nonfinite = e->nonfinite;

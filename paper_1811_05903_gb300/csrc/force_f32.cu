@@ -180,6 +180,9 @@ struct ForceArgs {
     double *__restrict__ partial;      // far field: per-CTA, per-segment partial sums
     double *__restrict__ item_part;    // near field: [items][3][T] partial sums
     uint32_t *__restrict__ nearbits;   // [ntile][words]: tile pair (I, J) is near
+    // per tile pair, the near 128 x 128 sub-blocks (bit 2 hI + hJ), or null:
+    // the near field then takes whole tile pairs
+    const uint8_t *__restrict__ submask;
     const int *__restrict__ near_cnt;  // [ntile] near tiles per target tile
     const int64_t *__restrict__ item_off;  // [ntile + 1] first work item of each target tile
     int64_t *near_meta;                // {chunk, items, work counter}
@@ -797,12 +800,22 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
                 const float hs = __fmul_rn(__fadd_rn(ci.w, cj.w), up);
                 soft = soft || gap2 <= __fmul_rn(hs, hs);
             }
-            if (soft)
-                near_tile_terms<TI, COMP, FOLD, true, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
-                                                      cz_);
-            else
-                near_tile_terms<TI, COMP, FOLD, false, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz, cx_, cy_,
-                                                       cz_);
+            // with sub-block masks only the near source halves of this target
+            // half (the far kernel took the others)
+            int j_begin = 0, j_end = T;
+            if (KI == 8 && a.submask) {
+                const int mk = a.submask[(d.bits_off + (itile - d.tile_off) * d.words) * 32 + jt] >> (2 * half);
+                j_begin = (mk & 1) ? 0 : T / 2;
+                j_end = (mk & 2) ? T : T / 2;
+            }
+            if (j_begin < j_end) {
+                if (soft)
+                    near_tile_terms<TI, COMP, FOLD, true, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz,
+                                                          cx_, cy_, cz_, j_begin, j_end);
+                else
+                    near_tile_terms<TI, COMP, FOLD, false, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz,
+                                                           cx_, cy_, cz_, j_begin, j_end);
+            }
             __syncwarp();  // every lane is done with buffer b before it is refilled
             jt = jn;
             if (NB == 2)
@@ -931,6 +944,8 @@ const VariantImpl kVariants[] = {
     // symmetric far field (force_sym.cu): 256-particle tiles, 4 compute warps
     {{8, 4, 4, true, "sym_ki8_w4", 2, 3}, nullptr, near_f32_kernel<8, true, kNearFold>, 0, near_smem_of<8>()},
     {{4, 4, 4, true, "sym_ki4_w4", 2, 4}, nullptr, near_f32_kernel<4, true, kNearFold>, 0, near_smem_of<4>()},
+    {{8, 4, 4, true, "sym_ki8s_w4", 2, 3, true}, nullptr, near_f32_kernel<8, true, kNearFold>, 0,
+     near_smem_of<8>()},
 };
 constexpr int kNumVariants = sizeof(kVariants) / sizeof(kVariants[0]);
 
@@ -960,6 +975,7 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
         d.blk_off = blocks;
         d.words = (d.ntile + 31) / 32;
         d.bits_off = bits;
+
         if (!sym)
             for (int64_t b = 0; b < d.ntile / W; ++b) starts.push_back(units + b * d.ntile);
         units += sym ? sym_units(d.ntile, W) : (d.ntile / W) * d.ntile;
@@ -967,12 +983,13 @@ ForcePlan plan_force_multi(int k, int num_sms, SimDesc *descs, int nsims, const 
         bits += d.ntile * d.words;
     }
     if (bits_words) *bits_words = bits;
+    p.mask_bytes = bits * 32;  // one byte per bit of the near bitmap
     p.niblk = blocks;
     p.units = units;
     cudaFuncSetAttribute(vi.near_fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)vi.near_smem);
     if (sym) {
         // persistent grid; every unit adds to fixed-point sums, no per-CTA partials
-        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(vi.v.KI, W, vi.v.ctas),
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>((int64_t)num_sms * sym_blocks_per_sm(vi.v.KI, W, vi.v.ctas, vi.v.sub),
                                                                     units));
         p.grid = (int)grid;
         p.smax = 0;
@@ -1024,6 +1041,7 @@ cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *parti
     a.partial = partial;
     a.item_part = nr.item_part;
     a.nearbits = nr.bits;
+    a.submask = (vi.v.form == 2 && vi.v.KI == 8 && s.tbox_hc) ? nr.submask : nullptr;
     a.near_cnt = nr.cnt;
     a.item_off = nr.item_off;
     a.near_meta = nr.meta;

@@ -71,6 +71,7 @@ struct SymArgs {
     const float4 *__restrict__ tbox_c;    // [ntile] (cx, cy, cz, hmax)
     const float4 *__restrict__ tbox_e;    // [ntile] (ex, ey, ez, tile mass)
     const uint32_t *__restrict__ nearbits;
+    const uint8_t *__restrict__ submask;  // sub-block near masks, or null (whole tile pairs)
     const float *__restrict__ tscale;     // [ntile] fixed-point scale
     unsigned long long *__restrict__ acc; // [3][np]
     int *nonfinite;
@@ -132,13 +133,123 @@ __device__ __forceinline__ void red_fixed(unsigned long long *addr, float v, flo
     atomicAdd(addr, (unsigned long long)__float2ll_rn(v * sc));
 }
 
-// One far unit for this warp: the warp's 256 targets against the 256 sources
-// of the staged tile S.  meta = (dc = c_I - c_J, M_J); myio holds the
-// negated target offsets.  Target sums go to the Kahan state myk; source sums
-// to the fixed-point array (scale scJ) of the source tile starting at
-// particle jbase.
+// One round of a unit (32 steps: the sources (r, k, g) for all groups g)
+// for the warp's targets in packed pairs [Q0, Q1): the two halves of a
+// 256-particle target tile are q = 0, 1 and q = 2, 3, so a round may skip
+// the half whose sub-block against this round's sources is near.
+template <int KI, int UNR, int Q0, int Q1>
+__device__ __forceinline__ void sym_round(const float4 *__restrict__ S, int r, const float2 ndx, const float2 ndy,
+                                          const float2 ndz, const float2 (&nox)[KI / 2], const float2 (&noy)[KI / 2],
+                                          const float2 (&noz)[KI / 2], float2 (&px)[KI / 2], float2 (&py)[KI / 2],
+                                          float2 (&pz)[KI / 2], const float2 (&mi)[KI / 2],
+                                          float4 *__restrict__ myk, int lane, int from, int64_t jbase, float scJ,
+                                          unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
+    constexpr int kNP = KI / 2;
+    // running sums of the sources of group (lane + step) mod 32: with 4 targets
+    // per lane the two packed halves are added before the rotation (6
+    // shuffles per step instead of 12; measured 2% faster there, 1% slower
+    // with 8 targets per lane)
+    constexpr bool kOne = KI == 4;
+    float2 Sx[kKJ], Sy[kKJ], Sz[kKJ];
+#pragma unroll
+    for (int k = 0; k < kKJ; ++k) Sx[k] = Sy[k] = Sz[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+    for (int h = 0; h < 32; h += kFold) {
+#pragma unroll UNR
+        for (int st = h; st < h + kFold; ++st) {
+            const int g = (lane + st) & 31;
+#pragma unroll
+            for (int k = 0; k < kKJ; ++k) {
+                const float4 *src = S + (r * kKJ + k) * 64 + g;
+                const float4 A = src[0], B = src[32];
+                const float2 xj = make_float2(A.x, A.y), yj = make_float2(A.z, A.w);
+                const float2 zj = make_float2(B.x, B.y), mj = make_float2(B.z, B.w);
+                // this step's targets on the two sources form a fresh partial that is
+                // added to the group's running sum once: the sum grows by 32 additions
+                // per round instead of 32 per packed pair
+                float2 tx, ty, tz;
+#pragma unroll
+                for (int q = Q0; q < Q1; ++q) {
+                    const float2 dx = __fadd2_rn(__fadd2_rn(xj, nox[q]), ndx);  // x_j - x_i
+                    const float2 dy = __fadd2_rn(__fadd2_rn(yj, noy[q]), ndy);
+                    const float2 dz = __fadd2_rn(__fadd2_rn(zj, noz[q]), ndz);
+                    float2 r2 = __fmul2_rn(dx, dx);
+                    r2 = __ffma2_rn(dy, dy, r2);
+                    r2 = __ffma2_rn(dz, dz, r2);
+                    const float2 w = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
+                    const float2 u = __fmul2_rn(__fmul2_rn(w, w), w);  // 1/r^3
+                    const float2 si = __fmul2_rn(u, mj);
+                    px[q] = __ffma2_rn(si, dx, px[q]);
+                    py[q] = __ffma2_rn(si, dy, py[q]);
+                    pz[q] = __ffma2_rn(si, dz, pz[q]);
+                    const float2 sj = __fmul2_rn(u, mi[q]);
+                    if (q == Q0) {
+                        tx = __fmul2_rn(sj, dx);
+                        ty = __fmul2_rn(sj, dy);
+                        tz = __fmul2_rn(sj, dz);
+                    } else {
+                        tx = __ffma2_rn(sj, dx, tx);
+                        ty = __ffma2_rn(sj, dy, ty);
+                        tz = __ffma2_rn(sj, dz, tz);
+                    }
+                }
+                if constexpr (kOne) {
+                    Sx[k].x = __fadd_rn(Sx[k].x, __fadd_rn(tx.x, tx.y));
+                    Sy[k].x = __fadd_rn(Sy[k].x, __fadd_rn(ty.x, ty.y));
+                    Sz[k].x = __fadd_rn(Sz[k].x, __fadd_rn(tz.x, tz.y));
+                } else {
+                    Sx[k] = __fadd2_rn(Sx[k], tx);
+                    Sy[k] = __fadd2_rn(Sy[k], ty);
+                    Sz[k] = __fadd2_rn(Sz[k], tz);
+                }
+            }
+            // pass the group's sums on: lane l takes over group (l + st + 1) mod 32
+#pragma unroll
+            for (int k = 0; k < kKJ; ++k) {
+                Sx[k].x = __shfl_sync(0xffffffffu, Sx[k].x, from);
+                Sy[k].x = __shfl_sync(0xffffffffu, Sy[k].x, from);
+                Sz[k].x = __shfl_sync(0xffffffffu, Sz[k].x, from);
+                if constexpr (!kOne) {
+                    Sx[k].y = __shfl_sync(0xffffffffu, Sx[k].y, from);
+                    Sy[k].y = __shfl_sync(0xffffffffu, Sy[k].y, from);
+                    Sz[k].y = __shfl_sync(0xffffffffu, Sz[k].y, from);
+                }
+            }
+        }
+        // fold the target partials into the compensated sums
+#pragma unroll
+        for (int q = Q0; q < Q1; ++q) {
+            float4 *K = myk + q * 32 + lane;
+            float4 kx = K[0], ky = K[kNP * 32], kz = K[2 * kNP * 32];
+            float2 hx = make_float2(kx.x, kx.y), cx = make_float2(kx.z, kx.w);
+            float2 hy = make_float2(ky.x, ky.y), cy = make_float2(ky.z, ky.w);
+            float2 hz = make_float2(kz.x, kz.y), cz = make_float2(kz.z, kz.w);
+            kahan2(hx, cx, px[q]);
+            kahan2(hy, cy, py[q]);
+            kahan2(hz, cz, pz[q]);
+            K[0] = make_float4(hx.x, hx.y, cx.x, cx.y);
+            K[kNP * 32] = make_float4(hy.x, hy.y, cy.x, cy.y);
+            K[2 * kNP * 32] = make_float4(hz.x, hz.y, cz.x, cz.y);
+            px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+        }
+    }
+    // this lane now holds its own group: sources (r, k, lane); the force on
+    // a source is minus the sum of m_i (x_j - x_i) / r^3
+#pragma unroll
+    for (int k = 0; k < kKJ; ++k) {
+        const int64_t idx = jbase + (r * kKJ + k) * 32 + lane;
+        red_fixed(acc + idx, -(Sx[k].x + Sx[k].y), scJ, nonfinite);
+        red_fixed(acc + np + idx, -(Sy[k].x + Sy[k].y), scJ, nonfinite);
+        red_fixed(acc + 2 * np + idx, -(Sz[k].x + Sz[k].y), scJ, nonfinite);
+    }
+}
+
+// One far unit for this warp without sub-blocks (every round over all the
+// warp's targets): the same terms and order as sym_far_unit with mask 0,
+// written as one loop nest (the round bodies of the sub-block kernel cost this
+// kernel 0.6-1.6% when it shared them).
 template <int KI, int UNR>
-__device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const float4 meta,
+__device__ __forceinline__ void sym_far_unit_plain(const float4 *__restrict__ S, const float4 meta,
                                              const float2 *__restrict__ myio, float4 *__restrict__ myk,
                                              const float2 (&mi)[KI / 2], int lane, int64_t jbase, float scJ,
                                              unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
@@ -263,10 +374,63 @@ __device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const
     }
 }
 
+// One far unit for this warp: the warp's 32 KI targets against the 32 KI
+// sources of the staged tile S.  meta = (dc = c_I - c_J, M_J); myio holds the
+// negated target offsets.  Target sums go to the Kahan state myk; source sums
+// to the fixed-point array (scale scJ) of the source tile starting at
+// particle jbase.  mask (256-particle tiles only): bit 2 hI + hJ set = the
+// sub-block of target half hI and source half hJ is near and left to the
+// near-field kernel.
+template <int KI, int UNR, bool SUB>
+__device__ __forceinline__ void sym_far_unit(const float4 *__restrict__ S, const float4 meta, int mask,
+                                             const float2 *__restrict__ myio, float4 *__restrict__ myk,
+                                             const float2 (&mi)[KI / 2], int lane, int64_t jbase, float scJ,
+                                             unsigned long long *__restrict__ acc, int64_t np, int *nonfinite) {
+    constexpr int kNP = KI / 2;
+    constexpr int kR = KI / kKJ;  // rounds of 32 steps (32 KI sources, kKJ per lane and step)
+    // The separation is formed as (o_j - o_i) - dc: the offsets are small (tile
+    // scale) and dc is exact, so d carries only rounding relative to itself.
+    // (Forming a shifted target s = o_i + dc once per unit would save one
+    // addition, but its rounding acts as a shift of the target that is the same
+    // for all its sources: a coherent error that does not average out.)
+    float2 nox[kNP], noy[kNP], noz[kNP];  // -o_i
+    float2 px[kNP], py[kNP], pz[kNP];     // FP32 target partials
+    const float2 ndx = make_float2(-meta.x, -meta.x), ndy = make_float2(-meta.y, -meta.y),
+                 ndz = make_float2(-meta.z, -meta.z);
+#pragma unroll
+    for (int q = 0; q < kNP; ++q) {
+        nox[q] = myio[(0 * kNP + q) * 32 + lane];
+        noy[q] = myio[(1 * kNP + q) * 32 + lane];
+        noz[q] = myio[(2 * kNP + q) * 32 + lane];
+        px[q] = py[q] = pz[q] = make_float2(0.f, 0.f);
+    }
+    const int from = (lane + 1) & 31;
+#pragma unroll 1
+    for (int r = 0; r < kR; ++r) {
+        if constexpr (KI == 8 && SUB) {
+            const int hJ = r / (kR / 2);  // source half of this round
+            const bool a0 = !((mask >> hJ) & 1), a1 = !((mask >> (2 + hJ)) & 1);
+            if (a0 && a1)
+                sym_round<KI, UNR, 0, kNP>(S, r, ndx, ndy, ndz, nox, noy, noz, px, py, pz, mi, myk, lane, from,
+                                           jbase, scJ, acc, np, nonfinite);
+            else if (a0)
+                sym_round<KI, UNR, 0, kNP / 2>(S, r, ndx, ndy, ndz, nox, noy, noz, px, py, pz, mi, myk, lane,
+                                               from, jbase, scJ, acc, np, nonfinite);
+            else if (a1)
+                sym_round<KI, UNR, kNP / 2, kNP>(S, r, ndx, ndy, ndz, nox, noy, noz, px, py, pz, mi, myk, lane,
+                                                 from, jbase, scJ, acc, np, nonfinite);
+        } else {
+            sym_round<KI, UNR, 0, kNP>(S, r, ndx, ndy, ndz, nox, noy, noz, px, py, pz, mi, myk, lane, from, jbase,
+                                       scJ, acc, np, nonfinite);
+        }
+    }
+}
+
 // Fill stage s = k mod NS with unit k of this CTA's range (cursor c): the W
-// warps' metadata (dc, M_J or -1 when that warp's tile pair is near) and the
-// bulk copy of the source tile.  Called by one whole warp.
-template <int KI, int W, int NS>
+// warps' metadata (dc, and M_J, or minus the near sub-block mask, or -16
+// when the pair is another unit's) and the bulk copy of the source tile.
+// Called by one whole warp.
+template <int KI, int W, int NS, bool SUB>
 __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> &c, int64_t k, float4 *sj,
                                           float4 *smeta, uint64_t *full, long long *issued, int lane) {
     constexpr int kT = 32 * KI;
@@ -276,12 +440,18 @@ __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> 
     if (lane < W) {
         const int64_t il = c.b * W + lane;
         const uint32_t word = a.nearbits[c.d.bits_off + il * c.d.words + (c.J >> 5)];
-        // near pairs and target tiles at or after J (their pair with J is another unit's)
-        const bool near = ((word >> (c.J & 31)) & 1u) || il >= c.J;
+        // w: M_J for a far tile pair; -mask (the near sub-blocks, 15: all) for a
+        // near one; -16 for target tiles at or after J (their pair with J is
+        // another unit's)
+        const bool near = (word >> (c.J & 31)) & 1u;
+        const bool other = il >= c.J;
+        int mask = 15;
+        if constexpr (SUB)
+            if (!other && near) mask = a.submask[(c.d.bits_off + il * c.d.words) * 32 + c.J];
         const float4 ci = a.tbox_c[c.d.tile_off + il], cj = a.tbox_c[jg];
         // exact: the tile centres lie on a common grid (staging)
         smeta[s * W + lane] = make_float4(__fsub_rn(ci.x, cj.x), __fsub_rn(ci.y, cj.y), __fsub_rn(ci.z, cj.z),
-                                          near ? -1.f : a.tbox_e[jg].w);
+                                          other ? -16.f : (near ? -(float)mask : a.tbox_e[jg].w));
     }
     __syncwarp();
     if (lane == 0) {
@@ -308,7 +478,7 @@ __device__ __forceinline__ void sym_issue(const SymArgs &a, const UnitCursor<W> 
 // CTA of each SM ran ~30% longer than the first.  Every chunk starts and
 // flushes its own target sums, so the result does not depend on which CTA
 // takes which chunk.
-template <int KI, int W, int NS, int MINB, int UNR>
+template <int KI, int W, int NS, int MINB, int UNR, bool SUB>
 __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) {
     constexpr int kT = 32 * KI;
     constexpr int kNP = KI / 2;
@@ -355,7 +525,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
         if (warp == 0) {
             UnitCursor<W> p = c;
             for (int64_t t = 0; t < NS && t < count; ++t) {
-                sym_issue<KI, W, NS>(a, p, k0 + t, sj, smeta, full, issued, lane);
+                sym_issue<KI, W, NS, SUB>(a, p, k0 + t, sj, smeta, full, issued, lane);
                 p.next(a.sims, a.nsims);
             }
         }
@@ -396,10 +566,17 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
                     break;
                 }
                 const float4 meta = smeta[s * W + warp];
-                if (meta.w >= 0.f) {
+                if constexpr (SUB) {
                     const int64_t jg = c.d.tile_off + c.J;
-                    sym_far_unit<KI, UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT,
-                                          a.tscale[jg], a.acc, a.np, a.nonfinite);
+                    // far: mask 0; partly near: the near sub-blocks; 15 (all near) or 16: skip
+                    const int mask = meta.w >= 0.f ? 0 : (int)(-meta.w);
+                    if (mask < 15)
+                        sym_far_unit<KI, UNR, SUB>(sj + (size_t)s * 2 * kT, meta, mask, myio, myk, mi, lane,
+                                                   jg * kT, a.tscale[jg], a.acc, a.np, a.nonfinite);
+                } else if (meta.w >= 0.f) {
+                    const int64_t jg = c.d.tile_off + c.J;
+                    sym_far_unit_plain<KI, UNR>(sj + (size_t)s * 2 * kT, meta, myio, myk, mi, lane, jg * kT,
+                                                a.tscale[jg], a.acc, a.np, a.nonfinite);
                 }
                 // done with the stage: the last warp refills it with unit k + NS of the chunk
                 __syncwarp();
@@ -412,7 +589,7 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
                 if (__shfl_sync(0xffffffffu, last, 0) && k - k0 + NS < count) {
                     UnitCursor<W> p = c;
                     for (int t = 0; t < NS; ++t) p.next(a.sims, a.nsims);
-                    sym_issue<KI, W, NS>(a, p, k + NS, sj, smeta, full, issued, lane);
+                    sym_issue<KI, W, NS, SUB>(a, p, k + NS, sj, smeta, full, issued, lane);
                 }
                 c.next(a.sims, a.nsims);
             }
@@ -450,6 +627,8 @@ __global__ void __launch_bounds__(W * 32, MINB) sym_far_kernel(const SymArgs a) 
 // One warp per tile row.
 template <int W>
 __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const float4 *__restrict__ tbox_e,
+                                    const float4 *__restrict__ hbox_c, const float4 *__restrict__ hbox_e,
+                                    uint8_t *__restrict__ submask,
                                     const SimDesc *__restrict__ sims, int nsims, int64_t ntile_all,
                                     float alpha2, uint32_t *__restrict__ bits, float *__restrict__ tscale,
                                     double *__restrict__ tinv, unsigned long long *stats) {
@@ -459,14 +638,38 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
     const SimDesc d = sims[sim_of_tile(sims, nsims, row)];
     const int64_t I = row - d.tile_off;
     const float4 ci = tbox_c[row], ei = tbox_e[row];
-    double bound = 0.0;
-    unsigned long long nn = 0;
+    double bound = 0.0, bh[2] = {0.0, 0.0};  // bh: per half of I when sub-blocks are classified
+    unsigned long long nn = 0;  // near tile pairs, or near sub-blocks (quarters of a pair)
     for (int64_t j0 = 0; j0 < d.ntile; j0 += 32) {
         const int64_t J = j0 + lane;
         bool near = false;
         if (J < d.ntile) {
             if (J == I) {
                 near = true;
+                if (submask) {
+                    submask[(d.bits_off + I * d.words) * 32 + J] = 15;
+                    nn += 3;  // with the 1 below: all four sub-blocks
+                }
+            } else if (submask) {
+                // 128 x 128 sub-blocks: bit 2 hI + hJ marks half hI of I against
+                // half hJ of J near; the far kernel takes the other sub-blocks
+                int mask = 0;
+#pragma unroll
+                for (int hI = 0; hI < 2; ++hI) {
+#pragma unroll
+                    for (int hJ = 0; hJ < 2; ++hJ) {
+                        const float4 a = hbox_c[2 * row + hI], ae = hbox_e[2 * row + hI];
+                        const float4 b = hbox_c[2 * (d.tile_off + J) + hJ], be = hbox_e[2 * (d.tile_off + J) + hJ];
+                        float gap2 = 0.f;
+                        if (tile_pair_near(a, ae, b, be, alpha2, &gap2, false))
+                            mask |= 1 << (2 * hI + hJ);
+                        else
+                            bh[hI] += (double)be.w / (double)gap2;
+                    }
+                }
+                near = mask != 0;
+                submask[(d.bits_off + I * d.words) * 32 + J] = (uint8_t)mask;
+                if (near) nn += __popc(mask) - 1;  // with the 1 below: the near sub-blocks
             } else {
                 const float4 cj = tbox_c[d.tile_off + J], ej = tbox_e[d.tile_off + J];
                 float gap2 = 0.f;
@@ -480,8 +683,12 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
     }
     for (int o = 16; o > 0; o >>= 1) {
         bound += __shfl_xor_sync(0xffffffffu, bound, o);
+        bh[0] += __shfl_xor_sync(0xffffffffu, bh[0], o);
+        bh[1] += __shfl_xor_sync(0xffffffffu, bh[1], o);
         nn += __shfl_xor_sync(0xffffffffu, nn, o);
     }
+    // with sub-blocks every particle of half hI sums at most bh[hI]
+    if (submask) bound = fmax(bh[0], bh[1]);
     if (lane == 0) {
         int e = -200;
         if (bound > 0.0) frexp(2.0 * bound, &e);  // 2 B < 2^e
@@ -491,7 +698,7 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
         tinv[row] = ldexp(1.0, -sh);
         if (stats) {
             atomicAdd(&stats[0], nn);
-            atomicAdd(&stats[1], (unsigned long long)d.ntile);
+            atomicAdd(&stats[1], (unsigned long long)d.ntile * (submask ? 4 : 1));
         }
     }
 }
@@ -536,11 +743,13 @@ constexpr size_t sym_smem_of() {
 using SymFn = void (*)(const SymArgs);
 
 // The built kernels: 256-particle tiles at 3 CTAs per SM (up to 168
-// registers), 128-particle tiles at 4 CTAs per SM (up to 128).
-SymFn sym_fn(int KI, int W, int ctas) {
+// registers), with or without 128 x 128 sub-blocks (the partial rounds are
+// compiled into their own kernel: the extra round bodies cost the plain kernel
+// 1.6% when they were in it), and 128-particle tiles at 4 CTAs per SM (up to 128).
+SymFn sym_fn(int KI, int W, int ctas, bool sub) {
     if (W != 4) return nullptr;
-    if (KI == 8 && ctas == 3) return sym_far_kernel<8, 4, kNS, 3, kUNR>;
-    if (KI == 4 && ctas == 4) return sym_far_kernel<4, 4, kNS, 4, kUNR>;
+    if (KI == 8 && ctas == 3) return sub ? sym_far_kernel<8, 4, kNS, 3, kUNR, true> : sym_far_kernel<8, 4, kNS, 3, kUNR, false>;
+    if (KI == 4 && ctas == 4 && !sub) return sym_far_kernel<4, 4, kNS, 4, kUNR, false>;
     return nullptr;
 }
 
@@ -556,8 +765,8 @@ size_t sym_smem_bytes(int KI, int W) {
     return KI == 8 ? sym_smem_of<8, 4>() : (KI == 4 ? sym_smem_of<4, 4>() : 0);
 }
 
-int sym_blocks_per_sm(int KI, int W, int ctas) {
-    SymFn fn = sym_fn(KI, W, ctas);
+int sym_blocks_per_sm(int KI, int W, int ctas, bool sub) {
+    SymFn fn = sym_fn(KI, W, ctas, sub);
     if (!fn) return 0;
     const size_t smem = sym_smem_bytes(KI, W);
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -572,8 +781,12 @@ cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const Near
     const int W = variant(p.variant).W;
     const unsigned blocks = (unsigned)((s.ntile * 32 + 255) / 256);
     if (W != 4) return cudaErrorInvalidValue;
-    sym_classify_kernel<4><<<blocks, 256, 0, st>>>(s.tbox_c, s.tbox_e, p.sims, p.nsims, s.ntile, alpha * alpha,
-                                                   nr.bits, nr.tscale, nr.tinv, stats);
+    // sub-block masks for the 256-particle variant when the staging has half boxes
+    const bool sub = variant(p.variant).KI == 8 && s.tbox_hc && nr.submask;
+    sym_classify_kernel<4><<<blocks, 256, 0, st>>>(s.tbox_c, s.tbox_e, sub ? s.tbox_hc : nullptr,
+                                                   sub ? s.tbox_he : nullptr, sub ? nr.submask : nullptr, p.sims,
+                                                   p.nsims, s.ntile, alpha * alpha, nr.bits, nr.tscale, nr.tinv,
+                                                   stats);
     return cudaGetLastError();
 }
 
@@ -581,13 +794,14 @@ cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScrat
                            long long wait_ns, cudaStream_t st) {
     const Variant &v = variant(p.variant);
     const int W = v.W;
-    SymFn fn = sym_fn(v.KI, W, v.ctas);
+    SymFn fn = sym_fn(v.KI, W, v.ctas, v.sub);
     if (!fn) return cudaErrorInvalidValue;
     SymArgs a;
     a.sdup = s.sdup;
     a.tbox_c = s.tbox_c;
     a.tbox_e = s.tbox_e;
     a.nearbits = nr.bits;
+    a.submask = (v.KI == 8 && s.tbox_hc) ? nr.submask : nullptr;
     a.tscale = nr.tscale;
     a.acc = nr.sym_acc;
     a.nonfinite = nr.nonfinite;

@@ -79,18 +79,18 @@ __device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
 // flags the lane; after the fold the flagged lanes add those pairs with the
 // spline of Eq. 4 (a warp vote: the whole warp calls this with the same SOFT).
 // Otherwise every pair is Newtonian and d != 0.
-// NSRC: sources in the staged tile (default: a tile of 32 KI).
+// NSRC: sources in the staged tile (default: a tile of 32 KI); only the
+// sources [j_begin, j_end) are summed (multiples of FOLD).
 template <int KI, bool COMP, int FOLD, bool SOFT, int NSRC = 32 * KI>
 __device__ __forceinline__ void near_tile_terms(
     const float4 *__restrict__ S, const float4 *__restrict__ Rr, const float2 (&nxs)[KI / 2],
     const float2 (&nys)[KI / 2], const float2 (&nzs)[KI / 2], const float2 (&nrx)[KI / 2],
     const float2 (&nry)[KI / 2], const float2 (&nrz)[KI / 2], const float2 (&hI)[KI / 2], float2 (&hx)[KI / 2],
     float2 (&hy)[KI / 2], float2 (&hz)[KI / 2], float2 (&cx_)[KI / 2], float2 (&cy_)[KI / 2],
-    float2 (&cz_)[KI / 2]) {
-    constexpr int T = NSRC;
+    float2 (&cz_)[KI / 2], int j_begin = 0, int j_end = NSRC) {
     constexpr int NPAIR = KI / 2;
 #pragma unroll 1
-    for (int f0 = 0; f0 < T; f0 += FOLD) {
+    for (int f0 = j_begin; f0 < j_end; f0 += FOLD) {
         float2 px[NPAIR], py[NPAIR], pz[NPAIR];
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {

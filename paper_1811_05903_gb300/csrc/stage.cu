@@ -31,6 +31,22 @@ __device__ T block_reduce(T v, T *sbuf, Op op) {
     return r;
 }
 
+// The same reduction over each half of the CTA (blockDim.x a multiple of 64):
+// every thread receives the result of its own half.
+template <typename T, typename Op>
+__device__ T half_reduce(T v, T *sbuf, Op op) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sbuf[wid] = v;
+    __syncthreads();
+    const int hw = ((blockDim.x + 31) >> 5) / 2;
+    const int w0 = wid < hw ? 0 : hw;
+    T r = sbuf[w0];
+    for (int w = w0 + 1; w < w0 + hw; ++w) r = op(r, sbuf[w]);
+    __syncthreads();
+    return r;
+}
+
 struct MinOp {
     __device__ double operator()(double a, double b) const { return fmin(a, b); }
 };
@@ -68,7 +84,8 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              float4 *__restrict__ jdup, float4 *__restrict__ rdup,
                              float4 *__restrict__ fdup, float4 *__restrict__ sdup,
                              const unsigned long long *__restrict__ qmax, double pscale, int qemin,
-                             float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e) {
+                             float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e,
+                             float4 *__restrict__ tbox_hc, float4 *__restrict__ tbox_he) {
     __shared__ double sbuf[32];
     const int64_t tile = blockIdx.x;
     const int64_t p = tile * T + threadIdx.x;
@@ -170,6 +187,32 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
         tbox_c[tile] = make_float4(cx, cy, cz, __double2float_ru(hmax));
         tbox_e[tile] = make_float4(__double2float_ru(ex), __double2float_ru(ey), __double2float_ru(ez),
                                    __double2float_rn(mass));
+    }
+    if (tbox_hc) {
+        // the boxes of the tile's two halves (first and last T/2 particles), for
+        // the near test of sub-blocks of tile pairs; centres need not lie on the
+        // grid (these boxes only classify)
+        const double hlox = half_reduce(valid ? px : DBL_MAX, sbuf, MinOp());
+        const double hloy = half_reduce(valid ? py : DBL_MAX, sbuf, MinOp());
+        const double hloz = half_reduce(valid ? pz : DBL_MAX, sbuf, MinOp());
+        const double hhix = half_reduce(valid ? px : -DBL_MAX, sbuf, MaxOp());
+        const double hhiy = half_reduce(valid ? py : -DBL_MAX, sbuf, MaxOp());
+        const double hhiz = half_reduce(valid ? pz : -DBL_MAX, sbuf, MaxOp());
+        const double hh = half_reduce(valid ? ph : 0.0, sbuf, MaxOp());
+        const double hm = half_reduce(valid ? pm : 0.0, sbuf, SumOp());
+        const bool hany = hlox <= hhix;
+        const float hcx = hany ? __double2float_rn(0.5 * (hlox + hhix)) : 0.f;
+        const float hcy = hany ? __double2float_rn(0.5 * (hloy + hhiy)) : 0.f;
+        const float hcz = hany ? __double2float_rn(0.5 * (hloz + hhiz)) : 0.f;
+        const double hex = half_reduce(valid ? fabs(px - (double)hcx) : 0.0, sbuf, MaxOp());
+        const double hey = half_reduce(valid ? fabs(py - (double)hcy) : 0.0, sbuf, MaxOp());
+        const double hez = half_reduce(valid ? fabs(pz - (double)hcz) : 0.0, sbuf, MaxOp());
+        if ((threadIdx.x & (blockDim.x / 2 - 1)) == 0) {
+            const int64_t hb = 2 * tile + (threadIdx.x >= blockDim.x / 2 ? 1 : 0);
+            tbox_hc[hb] = make_float4(hcx, hcy, hcz, __double2float_ru(hh));
+            tbox_he[hb] = make_float4(__double2float_ru(hex), __double2float_ru(hey), __double2float_ru(hez),
+                                      __double2float_rn(hm));
+        }
     }
 }
 
@@ -310,7 +353,8 @@ void launch_stage(const Staging &s, const double *x, const double *y, const doub
         absmax_kernel<<<152, 512, 0, st>>>(s.n, x, y, z, h, s.pscale, s.qmax);
     }
     stage_kernel<<<(unsigned)s.ntile, s.T, 0, st>>>(s.n, s.T, x, y, z, m, h, s.jdup, s.rdup, s.fdup, s.sdup,
-                                                    s.qmax, s.pscale, s.qemin, s.tbox_c, s.tbox_e);
+                                                    s.qmax, s.pscale, s.qemin, s.tbox_c, s.tbox_e, s.tbox_hc,
+                                                    s.tbox_he);
 }
 
 namespace {

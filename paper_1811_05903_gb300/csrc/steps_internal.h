@@ -52,6 +52,9 @@ struct Variant {
     // symmetric kernel: CTAs of 4 warps per SM it is compiled for (3 for
     // 256-particle tiles: up to 168 registers per thread; 4 for 128: up to 128)
     int ctas = 0;
+    // symmetric 256-particle tiles: classify 128 x 128 sub-blocks, so that only
+    // the near sub-blocks of a tile pair go to the near-field kernel
+    bool sub = false;
 };
 
 int num_variants();
@@ -84,6 +87,10 @@ struct Staging {
     int qemin = -1000;
     float4 *tbox_c = nullptr; // [ntile] (cx, cy, cz, hmax)
     float4 *tbox_e = nullptr; // [ntile] (ex, ey, ez, M) half extents (rounded up), tile mass
+    // [2 ntile] the same for the two halves of every tile, or null (the
+    // 256-particle symmetric variant classifies 128 x 128 sub-blocks)
+    float4 *tbox_hc = nullptr;
+    float4 *tbox_he = nullptr;
 };
 
 // One independent system inside the concatenated staging arrays.  A single
@@ -118,6 +125,11 @@ struct NearScratch {
     double *tinv = nullptr;                 // [ntile] 2^(E_t - 62)
     int *nonfinite = nullptr;               // set to 1 when a far-field partial is not finite
     unsigned long long *sym_next = nullptr; // chunk counter of the symmetric far kernel
+    // per ordered tile pair, bit 2 hI + hJ: the sub-block (half hI of I, half hJ
+    // of J) is near, laid out like the near bitmap with a byte per bit (row I
+    // of a system at (bits_off + I words) 32), or null
+    uint8_t *submask = nullptr;
+    int64_t mask_bytes = 0;                 // bytes of submask in use
 };
 
 // Stream-K plan for one FP32 force evaluation over one or more systems.
@@ -129,6 +141,7 @@ struct ForcePlan {
     int64_t units = 0;  // tile pairs, all systems
     int B_I = 0;
     size_t partial_elems = 0;  // grid * smax * 3 * B_I doubles
+    int64_t mask_bytes = 0;    // sub-block near masks of all systems (32 bytes per bitmap word)
     const SimDesc *sims = nullptr;  // device table
     int nsims = 1;
 };
@@ -141,7 +154,7 @@ ForcePlan plan_force(const Staging &s, int variant, int num_sms);
 int64_t sym_units(int64_t ntile, int W);
 size_t sym_smem_bytes(int KI, int W);
 // ctas: the variant's Variant::ctas (which compiled kernel)
-int sym_blocks_per_sm(int KI, int W, int ctas);
+int sym_blocks_per_sm(int KI, int W, int ctas, bool sub);
 // Near bitmap (all ordered tile pairs; each tile with itself is near),
 // per-tile fixed-point scales from a bound on the far-field sums, near/all counts.
 cudaError_t launch_sym_classify(const Staging &s, const ForcePlan &p, const NearScratch &nr, float alpha,

@@ -147,7 +147,7 @@ def test_precision_study_full_size_sampled():
     assert np.all(net <= 1e-6 * scale)
 
 
-SYM_VARIANTS = ["sym_ki8_w4", "sym_ki4_w4"]
+SYM_VARIANTS = ["sym_ki8_w4", "sym_ki4_w4", "sym_ki8s_w4"]
 
 
 def sym_variant(name="sym_ki8_w4"):
