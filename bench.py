@@ -41,7 +41,8 @@ L2_FLUSH_BYTES = 512 << 20
 # launch, measured by ncu (one pass, the launch-list run of this bench command)
 # for the named variant at the named size, with the kernel source as committed
 # alongside; any other variant or size reports null.
-FAR_TRAFFIC_BYTES = {("sym_ki8_w4", 1048576): 61_178_000}  # mean of 13 launches, 60.97-61.54 MB
+FAR_TRAFFIC_BYTES = {("sym_ki8s_w4", 1048576): 64_277_000,  # mean of 13 launches, 63.95-64.54 MB
+                     ("sym_ki8_w4", 1048576): 61_179_000}   # mean of 4 launches, 60.97-61.45 MB
 
 
 def peaks():
@@ -487,7 +488,8 @@ def run_ours(args):
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak, "traffic": FAR_TRAFFIC_BYTES.get((variant_name, n)),
                      "kernel": "%s (far field, %s)" % ("sym_far_kernel" if variant_name.startswith("sym") else "force_f32_kernel", variant_name),
-                     "basis": "%d flop/interaction x N^2 (1 - near tile-pair fraction %.4f) per launch / mean far-field "
+                     "basis": "%d flop/interaction x N^2 (1 - near fraction %.4f of the tile pairs, or of their 128 x 128 "
+                              "sub-blocks for sym_ki8s) per launch / mean far-field "
                               "launch time (CUDA events on the launching stream, %d launches); peak = %d SMs x 128 FP32 "
                               "lanes x 2 x %.0f MHz (FP32 FMA pipe, no measured FP32 peak on file)"
                               % (FLOP_PER_INTERACTION, near_frac, far_launches, props.multi_processor_count, max_mhz),
