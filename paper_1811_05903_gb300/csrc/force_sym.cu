@@ -813,8 +813,9 @@ cudaError_t launch_sym_far(const Staging &s, const ForcePlan &p, const NearScrat
     a.wait_ns = wait_ns;
     if (p.units <= 0) return cudaSuccess;
     if (!nr.sym_next) return cudaErrorInvalidValue;
-    // about 32 chunks per CTA: a finishing tail of ~1/32 of a CTA's share
-    const int64_t want = (int64_t)std::max(p.grid, 1) * 32;
+    // about 64 chunks per CTA: a finishing tail of ~1/64 of a CTA's share (16, 32 and
+    // 64 measured within 0.5% of each other at 262,144 and 2^20, 64 best)
+    const int64_t want = (int64_t)std::max(p.grid, 1) * 64;
     a.chunk = std::max<int64_t>(1, (p.units + want - 1) / want);
     a.next = nr.sym_next;
     cudaError_t e = cudaMemsetAsync(nr.sym_next, 0, sizeof(unsigned long long), st);
