@@ -652,10 +652,19 @@ __global__ void sym_classify_kernel(const float4 *__restrict__ tbox_c, const flo
                 }
             } else if (submask) {
                 // 128 x 128 sub-blocks: bit 2 hI + hJ marks half hI of I against
-                // half hJ of J near; the far kernel takes the other sub-blocks
+                // half hJ of J near; the far kernel takes the other sub-blocks.
+                // A tile pair that is far as a whole has far halves (their boxes
+                // lie inside the tiles'; the tile gap bounds both halves' sums).
+                const float4 cj = tbox_c[d.tile_off + J], ej = tbox_e[d.tile_off + J];
+                float tgap2 = 0.f;
+                const bool tnear = tile_pair_near(ci, ei, cj, ej, alpha2, &tgap2, false);
                 int mask = 0;
+                if (!tnear) {
+                    bh[0] += (double)ej.w / (double)tgap2;
+                    bh[1] += (double)ej.w / (double)tgap2;
+                }
 #pragma unroll
-                for (int hI = 0; hI < 2; ++hI) {
+                for (int hI = 0; hI < 2 && tnear; ++hI) {
 #pragma unroll
                     for (int hJ = 0; hJ < 2; ++hJ) {
                         const float4 a = hbox_c[2 * row + hI], ae = hbox_e[2 * row + hI];
