@@ -41,8 +41,8 @@ L2_FLUSH_BYTES = 512 << 20
 # launch, measured by ncu (one pass, the launch-list run of this bench command)
 # for the named variant at the named size, with the kernel source as committed
 # alongside; any other variant or size reports null.
-FAR_TRAFFIC_BYTES = {("sym_ki8s_w4", 1048576): 64_277_000,  # mean of 13 launches, 63.95-64.54 MB
-                     ("sym_ki8_w4", 1048576): 61_179_000}   # mean of 4 launches, 60.97-61.45 MB
+FAR_TRAFFIC_BYTES = {("sym_ki8s_w4", 1048576): 64_244_000,  # mean of 13 launches, 63.96-64.60 MB
+                     ("sym_ki8_w4", 1048576): 61_091_000}   # mean of 4 launches, 60.93-61.23 MB
 
 
 def peaks():
