@@ -19,10 +19,10 @@
 //  * A unit is (target block b of W tiles, source tile J) with J after the
 //    block's first tile; warp w takes target tile b W + w only when it
 //    precedes J, so each pair of distinct tiles is one unit of one warp.  A
-//    persistent grid splits the units evenly (stream-K); source tiles stream
-//    into a shared-memory ring with TMA bulk copies (cp.async.bulk completing
-//    on mbarriers), each stage refilled by the last warp done with it; warp w
-//    owns target tile b W + w.
+//    persistent grid takes fixed chunks of consecutive units from a global
+//    counter; source tiles stream into a shared-memory ring with TMA bulk
+//    copies (cp.async.bulk completing on mbarriers), each stage refilled by
+//    the last warp done with it; warp w owns target tile b W + w.
 //  * Inside a warp, lane l holds 8 targets (particles l + 32 t) as 4 packed
 //    pairs (FFMA2).  The source tile is processed in 4 rounds of 32 steps; at
 //    step s lane l takes the 2 sources of group (l + s) mod 32, so no two
