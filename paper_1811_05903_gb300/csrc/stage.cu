@@ -31,22 +31,6 @@ __device__ T block_reduce(T v, T *sbuf, Op op) {
     return r;
 }
 
-// The same reduction over each half of the CTA (blockDim.x a multiple of 64):
-// every thread receives the result of its own half.
-template <typename T, typename Op>
-__device__ T half_reduce(T v, T *sbuf, Op op) {
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (int o = 16; o > 0; o >>= 1) v = op(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (lane == 0) sbuf[wid] = v;
-    __syncthreads();
-    const int hw = ((blockDim.x + 31) >> 5) / 2;
-    const int w0 = wid < hw ? 0 : hw;
-    T r = sbuf[w0];
-    for (int w = w0 + 1; w < w0 + hw; ++w) r = op(r, sbuf[w]);
-    __syncthreads();
-    return r;
-}
-
 struct MinOp {
     __device__ double operator()(double a, double b) const { return fmin(a, b); }
 };
@@ -56,6 +40,42 @@ struct MaxOp {
 struct SumOp {
     __device__ double operator()(double a, double b) const { return a + b; }
 };
+
+// Order-preserving integer key of a finite double (a < b <=> key(a) < key(b)):
+// the staging kernel takes its minima and maxima on these keys, which is exact
+// and runs on the integer pipe instead of GB300's narrow FP64 pipe.
+__device__ __forceinline__ long long ord_key(double v) {
+    const long long b = __double_as_longlong(v);
+    return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+__device__ __forceinline__ double key_value(long long k) {
+    return __longlong_as_double(k >= 0 ? k : (k ^ 0x7fffffffffffffffLL));
+}
+
+// Warp partials of K keys (xor tree, the same tree as block_reduce): key k
+// takes the minimum when (kmin >> k) & 1, else the maximum.  Lane 0 stores
+// the warp's results in red[k][warp]; the caller combines the warps after a
+// barrier.
+template <int K>
+__device__ __forceinline__ void warp_keys(long long (&v)[K], unsigned kmin, long long (*red)[32]) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int k = 0; k < K; ++k) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const long long u = __shfl_xor_sync(0xffffffffu, v[k], o);
+            v[k] = ((kmin >> k) & 1) ? (u < v[k] ? u : v[k]) : (u > v[k] ? u : v[k]);
+        }
+        if (lane == 0) red[k][wid] = v[k];
+    }
+}
+
+// Warps [w0, w1) of a stored key row combined in warp order.
+__device__ __forceinline__ long long combine_keys(const long long *row, int w0, int w1, bool is_min) {
+    long long r = row[w0];
+    for (int w = w0 + 1; w < w1; ++w) r = is_min ? (row[w] < r ? row[w] : r) : (row[w] > r ? row[w] : r);
+    return r;
+}
 
 // One CTA per tile, blockDim.x == T.
 // Largest |coordinate| of the real particles into *out (the bit pattern of a
@@ -74,8 +94,10 @@ __global__ void absmax_kernel(int64_t n, const double *__restrict__ x, const dou
 // Tile centre component rounded to the grid q (q = 0: no rounding).  With
 // max|x| < 2^e and q = 2^(e-22), a rounded centre has at most 23 significant
 // bits and the difference of two centres at most 24: both exact in FP32.
-__device__ __forceinline__ float grid_centre(double mid, double q) {
-    return q > 0.0 ? (float)(rint(mid / q) * q) : __double2float_rn(mid);
+// qinv = 1/q (both powers of two: mid * qinv equals mid / q, without an FP64
+// division).
+__device__ __forceinline__ float grid_centre(double mid, double q, double qinv) {
+    return q > 0.0 ? (float)(rint(mid * qinv) * q) : __double2float_rn(mid);
 }
 
 __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
@@ -86,7 +108,11 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
                              const unsigned long long *__restrict__ qmax, double pscale, int qemin,
                              float4 *__restrict__ tbox_c, float4 *__restrict__ tbox_e,
                              float4 *__restrict__ tbox_hc, float4 *__restrict__ tbox_he) {
-    __shared__ double sbuf[32];
+    // per-warp partials: the bounding box, largest softening and mass, then
+    // the extents (the whole tile's in 0-2, the halves' in 3-5)
+    __shared__ long long kbox[7][32];
+    __shared__ double kmass[32];
+    __shared__ long long kext[6][32];
     const int64_t tile = blockIdx.x;
     const int64_t p = tile * T + threadIdx.x;
     const bool valid = p < n && !(h[p] < 0.0);  // negative softening marks padding
@@ -98,17 +124,32 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
         pm = m[p];
         ph = h[p] * pscale;
     }
-    const double lox = block_reduce(valid ? px : DBL_MAX, sbuf, MinOp());
-    const double loy = block_reduce(valid ? py : DBL_MAX, sbuf, MinOp());
-    const double loz = block_reduce(valid ? pz : DBL_MAX, sbuf, MinOp());
-    const double hix = block_reduce(valid ? px : -DBL_MAX, sbuf, MaxOp());
-    const double hiy = block_reduce(valid ? py : -DBL_MAX, sbuf, MaxOp());
-    const double hiz = block_reduce(valid ? pz : -DBL_MAX, sbuf, MaxOp());
-    const double hmax = block_reduce(valid ? ph : 0.0, sbuf, MaxOp());
-    const double mass = block_reduce(valid ? pm : 0.0, sbuf, SumOp());
+    const int wid = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+    // the tile's warps, and the warps of this thread's half (first or last T/2)
+    const int hw = nw / 2, w0 = wid < hw ? 0 : hw;
+    {
+        long long kv[7] = {ord_key(valid ? px : DBL_MAX),  ord_key(valid ? py : DBL_MAX),
+                           ord_key(valid ? pz : DBL_MAX),  ord_key(valid ? px : -DBL_MAX),
+                           ord_key(valid ? py : -DBL_MAX), ord_key(valid ? pz : -DBL_MAX),
+                           ord_key(valid ? ph : 0.0)};
+        warp_keys<7>(kv, 0x7u, kbox);
+        double sm = valid ? pm : 0.0;
+        for (int o = 16; o > 0; o >>= 1) sm += __shfl_xor_sync(0xffffffffu, sm, o);
+        if ((threadIdx.x & 31) == 0) kmass[wid] = sm;
+    }
+    __syncthreads();
+    const double lox = key_value(combine_keys(kbox[0], 0, nw, true));
+    const double loy = key_value(combine_keys(kbox[1], 0, nw, true));
+    const double loz = key_value(combine_keys(kbox[2], 0, nw, true));
+    const double hix = key_value(combine_keys(kbox[3], 0, nw, false));
+    const double hiy = key_value(combine_keys(kbox[4], 0, nw, false));
+    const double hiz = key_value(combine_keys(kbox[5], 0, nw, false));
+    const double hmax = key_value(combine_keys(kbox[6], 0, nw, false));
+    double mass = kmass[0];
+    for (int w = 1; w < nw; ++w) mass += kmass[w];
     const bool any = lox <= hix;  // tile holds at least one real particle
     // FP32 centre (exactly representable), FP64 offsets rounded once to FP32
-    double q = 0.0;
+    double q = 0.0, qinv = 0.0;
     if (qmax) {
         const double amax = __longlong_as_double((long long)*qmax);
         int e = 0;
@@ -121,15 +162,46 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
             e = qemin;
             grid = true;
         }
-        if (grid) q = ldexp(1.0, e - 22);
+        if (grid) {
+            q = ldexp(1.0, e - 22);
+            qinv = ldexp(1.0, 22 - e);
+        }
     }
-    const float cx = any ? grid_centre(0.5 * (lox + hix), q) : 0.f;
-    const float cy = any ? grid_centre(0.5 * (loy + hiy), q) : 0.f;
-    const float cz = any ? grid_centre(0.5 * (loz + hiz), q) : 0.f;
+    const float cx = any ? grid_centre(0.5 * (lox + hix), q, qinv) : 0.f;
+    const float cy = any ? grid_centre(0.5 * (loy + hiy), q, qinv) : 0.f;
+    const float cz = any ? grid_centre(0.5 * (loz + hiz), q, qinv) : 0.f;
     const double dx = px - (double)cx, dy = py - (double)cy, dz = pz - (double)cz;
-    const double ex = block_reduce(valid ? fabs(dx) : 0.0, sbuf, MaxOp());
-    const double ey = block_reduce(valid ? fabs(dy) : 0.0, sbuf, MaxOp());
-    const double ez = block_reduce(valid ? fabs(dz) : 0.0, sbuf, MaxOp());
+    // the halves' boxes (sub-block near tests): centres need not lie on the
+    // grid, these boxes only classify
+    float hcx = 0.f, hcy = 0.f, hcz = 0.f, hh = 0.f, hm = 0.f;
+    if (tbox_hc) {
+        const double hlox = key_value(combine_keys(kbox[0], w0, w0 + hw, true));
+        const double hloy = key_value(combine_keys(kbox[1], w0, w0 + hw, true));
+        const double hloz = key_value(combine_keys(kbox[2], w0, w0 + hw, true));
+        const double hhix = key_value(combine_keys(kbox[3], w0, w0 + hw, false));
+        const double hhiy = key_value(combine_keys(kbox[4], w0, w0 + hw, false));
+        const double hhiz = key_value(combine_keys(kbox[5], w0, w0 + hw, false));
+        hh = __double2float_ru(key_value(combine_keys(kbox[6], w0, w0 + hw, false)));
+        double hms = kmass[w0];
+        for (int w = w0 + 1; w < w0 + hw; ++w) hms += kmass[w];
+        hm = __double2float_rn(hms);
+        if (hlox <= hhix) {
+            hcx = __double2float_rn(0.5 * (hlox + hhix));
+            hcy = __double2float_rn(0.5 * (hloy + hhiy));
+            hcz = __double2float_rn(0.5 * (hloz + hhiz));
+        }
+    }
+    {
+        long long kv[6] = {ord_key(valid ? fabs(dx) : 0.0), ord_key(valid ? fabs(dy) : 0.0),
+                           ord_key(valid ? fabs(dz) : 0.0), ord_key(valid ? fabs(px - (double)hcx) : 0.0),
+                           ord_key(valid ? fabs(py - (double)hcy) : 0.0),
+                           ord_key(valid ? fabs(pz - (double)hcz) : 0.0)};
+        warp_keys<6>(kv, 0u, kext);
+    }
+    __syncthreads();
+    const double ex = key_value(combine_keys(kext[0], 0, nw, false));
+    const double ey = key_value(combine_keys(kext[1], 0, nw, false));
+    const double ez = key_value(combine_keys(kext[2], 0, nw, false));
     float ox, oy, oz, rx, ry, rz, fm, fh;
     if (valid) {
         ox = __double2float_rn(dx);
@@ -188,31 +260,13 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
         tbox_e[tile] = make_float4(__double2float_ru(ex), __double2float_ru(ey), __double2float_ru(ez),
                                    __double2float_rn(mass));
     }
-    if (tbox_hc) {
-        // the boxes of the tile's two halves (first and last T/2 particles), for
-        // the near test of sub-blocks of tile pairs; centres need not lie on the
-        // grid (these boxes only classify)
-        const double hlox = half_reduce(valid ? px : DBL_MAX, sbuf, MinOp());
-        const double hloy = half_reduce(valid ? py : DBL_MAX, sbuf, MinOp());
-        const double hloz = half_reduce(valid ? pz : DBL_MAX, sbuf, MinOp());
-        const double hhix = half_reduce(valid ? px : -DBL_MAX, sbuf, MaxOp());
-        const double hhiy = half_reduce(valid ? py : -DBL_MAX, sbuf, MaxOp());
-        const double hhiz = half_reduce(valid ? pz : -DBL_MAX, sbuf, MaxOp());
-        const double hh = half_reduce(valid ? ph : 0.0, sbuf, MaxOp());
-        const double hm = half_reduce(valid ? pm : 0.0, sbuf, SumOp());
-        const bool hany = hlox <= hhix;
-        const float hcx = hany ? __double2float_rn(0.5 * (hlox + hhix)) : 0.f;
-        const float hcy = hany ? __double2float_rn(0.5 * (hloy + hhiy)) : 0.f;
-        const float hcz = hany ? __double2float_rn(0.5 * (hloz + hhiz)) : 0.f;
-        const double hex = half_reduce(valid ? fabs(px - (double)hcx) : 0.0, sbuf, MaxOp());
-        const double hey = half_reduce(valid ? fabs(py - (double)hcy) : 0.0, sbuf, MaxOp());
-        const double hez = half_reduce(valid ? fabs(pz - (double)hcz) : 0.0, sbuf, MaxOp());
-        if ((threadIdx.x & (blockDim.x / 2 - 1)) == 0) {
-            const int64_t hb = 2 * tile + (threadIdx.x >= blockDim.x / 2 ? 1 : 0);
-            tbox_hc[hb] = make_float4(hcx, hcy, hcz, __double2float_ru(hh));
-            tbox_he[hb] = make_float4(__double2float_ru(hex), __double2float_ru(hey), __double2float_ru(hez),
-                                      __double2float_rn(hm));
-        }
+    if (tbox_hc && (threadIdx.x & (blockDim.x / 2 - 1)) == 0) {
+        const int64_t hb = 2 * tile + (threadIdx.x >= blockDim.x / 2 ? 1 : 0);
+        const double hex = key_value(combine_keys(kext[3], w0, w0 + hw, false));
+        const double hey = key_value(combine_keys(kext[4], w0, w0 + hw, false));
+        const double hez = key_value(combine_keys(kext[5], w0, w0 + hw, false));
+        tbox_hc[hb] = make_float4(hcx, hcy, hcz, hh);
+        tbox_he[hb] = make_float4(__double2float_ru(hex), __double2float_ru(hey), __double2float_ru(hez), hm);
     }
 }
 
