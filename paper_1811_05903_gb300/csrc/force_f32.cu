@@ -725,7 +725,8 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
         const float4 ci = a.tbox_c[itile];
         const float4 ei = a.tbox_e[itile];
         const int64_t ibase = itile * T + half * 32 * TI + lane * TI;
-        float2 xi[NPAIR], yi[NPAIR], zi[NPAIR], rxi[NPAIR], ryi[NPAIR], rzi[NPAIR], hI[NPAIR];
+        float2 xi[NPAIR], yi[NPAIR], zi[NPAIR], rxi[NPAIR], ryi[NPAIR], rzi[NPAIR];
+        const float4 *RI = a.rdup + 2 * ibase;  // this lane's targets: residuals and h
 #pragma unroll
         for (int q = 0; q < NPAIR; ++q) {
             const float4 p0 = a.jdup[2 * (ibase + 2 * q)], p0z = a.jdup[2 * (ibase + 2 * q) + 1];
@@ -738,7 +739,6 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
             rxi[q] = make_float2(r0.x, r1.x);
             ryi[q] = make_float2(r0.z, r1.z);
             rzi[q] = make_float2(r0z.x, r1z.x);
-            hI[q] = make_float2(r0z.z, r1z.z);
         }
         float2 hx[NPAIR], hy[NPAIR], hz[NPAIR], cx_[NPAIR], cy_[NPAIR], cz_[NPAIR];
 #pragma unroll
@@ -809,12 +809,23 @@ __global__ void __launch_bounds__(32 * kNearWarps) near_f32_kernel(const ForceAr
                 j_end = (mk & 2) ? T : T / 2;
             }
             if (j_begin < j_end) {
-                if (soft)
-                    near_tile_terms<TI, COMP, FOLD, true, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz,
-                                                          cx_, cy_, cz_, j_begin, j_end);
-                else
-                    near_tile_terms<TI, COMP, FOLD, false, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hI, hx, hy, hz,
-                                                           cx_, cy_, cz_, j_begin, j_end);
+                if (soft) {
+                    // (h_i + the source tile's largest h)^2: at least (h_i + h_j)^2 for
+                    // every source (rounding is monotone, the tile's h is rounded up)
+                    float2 hT2[NPAIR];
+#pragma unroll
+                    for (int q = 0; q < NPAIR; ++q) {
+                        const float h0 = __fadd_rn(RI[2 * (2 * q) + 1].z, cj.w);
+                        const float h1 = __fadd_rn(RI[2 * (2 * q + 1) + 1].z, cj.w);
+                        hT2[q] = make_float2(__fmul_rn(h0, h0), __fmul_rn(h1, h1));
+                    }
+                    near_tile_terms<TI, COMP, FOLD, true, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, hT2, RI, hx, hy,
+                                                          hz, cx_, cy_, cz_, j_begin, j_end);
+                } else {
+                    const float2 none[NPAIR] = {};
+                    near_tile_terms<TI, COMP, FOLD, false, T>(S, Rr, nxs, nys, nzs, nrx, nry, nrz, none, RI, hx,
+                                                           hy, hz, cx_, cy_, cz_, j_begin, j_end);
+                }
             }
             __syncwarp();  // every lane is done with buffer b before it is refilled
             jt = jn;

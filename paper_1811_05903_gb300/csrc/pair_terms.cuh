@@ -75,17 +75,20 @@ __device__ __forceinline__ void kahan1(float &hi, float &nc, const float p) {
 // pairs), folded into the targets' sums every FOLD sources.  Each source is
 // read once from shared memory for all pairs.  SOFT: some pair may lie inside
 // h_i + h_j (or the tile pair is a tile with itself): the packed loop leaves
-// every pair with r^2 <= (h_i + h_j)^2 out (self pairs, r = 0, among them) and
-// flags the lane; after the fold the flagged lanes add those pairs with the
-// spline of Eq. 4 (a warp vote: the whole warp calls this with the same SOFT).
-// Otherwise every pair is Newtonian and d != 0.
+// every pair with r^2 <= hT2 out, hT2 = (h_i + the source tile's largest h)^2
+// (so every pair inside h_i + h_j, and the self pairs, r = 0), and flags the
+// lane; after the fold the flagged lanes add those pairs, with the spline of
+// Eq. 4 where r < h_i + h_j (h_i from RI) and the Newtonian term elsewhere
+// (a warp vote: the whole warp calls this with the same SOFT).  Otherwise
+// every pair is Newtonian and d != 0.
 // NSRC: sources in the staged tile (default: a tile of 32 KI); only the
 // sources [j_begin, j_end) are summed (multiples of FOLD).
 template <int KI, bool COMP, int FOLD, bool SOFT, int NSRC = 32 * KI>
 __device__ __forceinline__ void near_tile_terms(
     const float4 *__restrict__ S, const float4 *__restrict__ Rr, const float2 (&nxs)[KI / 2],
     const float2 (&nys)[KI / 2], const float2 (&nzs)[KI / 2], const float2 (&nrx)[KI / 2],
-    const float2 (&nry)[KI / 2], const float2 (&nrz)[KI / 2], const float2 (&hI)[KI / 2], float2 (&hx)[KI / 2],
+    const float2 (&nry)[KI / 2], const float2 (&nrz)[KI / 2], const float2 (&hT2)[KI / 2],
+    const float4 *__restrict__ RI, float2 (&hx)[KI / 2],
     float2 (&hy)[KI / 2], float2 (&hz)[KI / 2], float2 (&cx_)[KI / 2], float2 (&cy_)[KI / 2],
     float2 (&cz_)[KI / 2], int j_begin = 0, int j_end = NSRC) {
     constexpr int NPAIR = KI / 2;
@@ -120,9 +123,7 @@ __device__ __forceinline__ void near_tile_terms(
                 r2 = __ffma2_rn(dz, dz, r2);
                 float2 ri = make_float2(rsqrt_approx(r2.x), rsqrt_approx(r2.y));
                 if (SOFT) {
-                    const float2 H = __fadd2_rn(hI[q], make_float2(RB.z, RB.w));
-                    const float2 H2 = __fmul2_rn(H, H);
-                    const bool ix = r2.x <= H2.x, iy = r2.y <= H2.y;
+                    const bool ix = r2.x <= hT2[q].x, iy = r2.y <= hT2[q].y;
                     inner = inner | ix | iy;
                     ri.x = ix ? 0.f : ri.x;
                     ri.y = iy ? 0.f : ri.y;
@@ -150,9 +151,10 @@ __device__ __forceinline__ void near_tile_terms(
                         const float dz = __fadd_rn(__fadd_rn(e ? B.y : B.x, e ? nzs[q].y : nzs[q].x),
                                                    __fadd_rn(e ? RB.y : RB.x, e ? nrz[q].y : nrz[q].x));
                         const float r2 = __fmaf_rn(dz, dz, __fmaf_rn(dy, dy, __fmul_rn(dx, dx)));
-                        const float H = __fadd_rn(e ? hI[q].y : hI[q].x, e ? RB.w : RB.z);
-                        const float H2 = __fmul_rn(H, H);
-                        if (r2 <= H2 && r2 > 0.f) {
+                        if (r2 <= (e ? hT2[q].y : hT2[q].x) && r2 > 0.f) {
+                            // RI: this lane's targets in the (rx, rx, ry, ry), (rz, rz, h, h) layout
+                            const float H = __fadd_rn(RI[2 * (2 * q + e) + 1].z, e ? RB.w : RB.z);
+                            const float H2 = __fmul_rn(H, H);
                             const float ri = rsqrt_approx(r2);
                             const float g = (r2 >= H2) ? ri * ri * ri : spline_over_r_f32(r2 * ri, H);
                             const float sc = (e ? B.w : B.z) * g;
