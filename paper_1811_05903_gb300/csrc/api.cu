@@ -529,7 +529,7 @@ steps_status init_impl(steps_ctx *c, const double *pos, const double *vel, const
     c->srt.npow2 = std::max<int64_t>(p2, 2);
     STEPS_TRY(alloc_n(c, &c->srt.keys, c->srt.npow2));
     STEPS_TRY(alloc_n(c, &c->srt.vals, c->srt.npow2));
-    STEPS_TRY(alloc_n(c, &c->srt.bbox, 8));
+    STEPS_TRY(alloc_n(c, &c->srt.bbox, 8 + 6 * 256));  // the box, then the per-CTA partials of morton_sort
     STEPS_TRY(alloc_n(c, &c->srt.tmp, n));
     STEPS_TRY(alloc_n(c, &c->srt.tmpi, n));
 

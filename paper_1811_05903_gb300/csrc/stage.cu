@@ -6,6 +6,7 @@
 // tile's FP32 centre (positions "relative to tile centres"), plus the tile's
 // half-extents and largest softening, which the force kernel uses to prove a
 // whole tile pair Newtonian (r >= h_i + h_j for every pair, Eq. 4 branch 3).
+#include <algorithm>
 #include <cfloat>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -272,26 +273,39 @@ __global__ void stage_kernel(int64_t n, int T, const double *__restrict__ x,
 
 // ---------------- Morton sort ----------------
 
-__global__ void bbox_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
-                            const double *__restrict__ z, double *__restrict__ bbox) {
-    // single CTA; deterministic
-    __shared__ double sbuf[32];
-    double lo[3] = {DBL_MAX, DBL_MAX, DBL_MAX}, hi[3] = {-DBL_MAX, -DBL_MAX, -DBL_MAX};
-    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+// Bounding box of the positions in two passes: per-CTA minima and maxima on
+// order-preserving integer keys (exact, and on the integer pipe; NaN entries
+// are skipped as fmin / fmax would), then one warp combines the CTAs in
+// order.  part: [6][gridDim.x] keys.
+constexpr int kBoxCtas = 256;
+
+__global__ void bbox_partial_kernel(int64_t n, const double *__restrict__ x, const double *__restrict__ y,
+                                    const double *__restrict__ z, long long *__restrict__ part) {
+    __shared__ long long red[6][32];
+    long long k[6];
+    for (int c = 0; c < 3; ++c) {
+        k[c] = ord_key(DBL_MAX);
+        k[3 + c] = ord_key(-DBL_MAX);
+    }
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const double v[3] = {x[i], y[i], z[i]};
-        for (int k = 0; k < 3; ++k) {
-            lo[k] = fmin(lo[k], v[k]);
-            hi[k] = fmax(hi[k], v[k]);
+        for (int c = 0; c < 3; ++c) {
+            if (!(v[c] == v[c])) continue;
+            const long long q = ord_key(v[c]);
+            k[c] = q < k[c] ? q : k[c];
+            k[3 + c] = q > k[3 + c] ? q : k[3 + c];
         }
     }
-    for (int k = 0; k < 3; ++k) {
-        const double a = block_reduce(lo[k], sbuf, MinOp());
-        const double b = block_reduce(hi[k], sbuf, MaxOp());
-        if (threadIdx.x == 0) {
-            bbox[k] = a;
-            bbox[3 + k] = b;
-        }
-    }
+    warp_keys<6>(k, 0x7u, red);
+    __syncthreads();
+    if (threadIdx.x < 6)
+        part[threadIdx.x * gridDim.x + blockIdx.x] =
+            combine_keys(red[threadIdx.x], 0, (blockDim.x + 31) >> 5, threadIdx.x < 3);
+}
+
+__global__ void bbox_final_kernel(int G, const long long *__restrict__ part, double *__restrict__ bbox) {
+    const int c = threadIdx.x;
+    if (c < 6) bbox[c] = key_value(combine_keys(part + (size_t)c * G, 0, G, c < 3));
 }
 
 __device__ __forceinline__ unsigned long long spread21(unsigned long long v) {
@@ -505,8 +519,12 @@ cudaError_t ensemble_sort(int nsims, const int64_t *off, int64_t np_total, const
 cudaError_t morton_sort(int64_t n, const double *x, const double *y, const double *z,
                         SortScratch &s, cudaStream_t st, int *launches) {
     const int64_t np2 = s.npow2;
-    int count = 2;
-    bbox_kernel<<<1, 1024, 0, st>>>(n, x, y, z, s.bbox);
+    int count = 3;
+    // the per-CTA partials live after the box itself (bbox holds 8 + 6 kBoxCtas words)
+    const int G = (int)std::min<int64_t>(kBoxCtas, std::max<int64_t>(1, (n + 255) / 256));
+    long long *part = reinterpret_cast<long long *>(s.bbox + 8);
+    bbox_partial_kernel<<<G, 256, 0, st>>>(n, x, y, z, part);
+    bbox_final_kernel<<<1, 32, 0, st>>>(G, part, s.bbox);
     morton_kernel<<<blocks_for(np2, 256), 256, 0, st>>>(n, np2, x, y, z, s.bbox, s.keys, s.vals);
     for (int64_t k = 2; k <= np2; k <<= 1) {
         int64_t j = k >> 1;

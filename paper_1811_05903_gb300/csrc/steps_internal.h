@@ -271,7 +271,7 @@ struct SortScratch {
     int64_t npow2 = 0;
     unsigned long long *keys = nullptr;
     unsigned int *vals = nullptr;
-    double *bbox = nullptr;   // [6] min xyz, max xyz
+    double *bbox = nullptr;   // [6] min xyz, max xyz (morton_sort: [8 + 6 x 256], partials after the box)
     double *tmp = nullptr;    // [n] gather buffer
     int64_t *tmpi = nullptr;  // [n]
 };
