@@ -99,7 +99,7 @@ struct Staging {
 struct SimDesc {
     int64_t tile_off;  // first global tile of the system
     int64_t ntile;     // its tiles (a multiple of the block's W)
-    int64_t unit_off;  // its first stream-K unit; units = (ntile / W) * ntile
+    int64_t unit_off;  // its first far-field unit (one-sided: (ntile / W) * ntile units; symmetric: sym_units)
     int64_t blk_off;   // its first target block in the global block order
     int64_t bits_off;  // first word of its near bitmap, [ntile][words]
     int64_t words;     // bitmap words per row, (ntile + 31) / 32
@@ -171,10 +171,11 @@ ForcePlan plan_force_multi(int variant, int num_sms, SimDesc *descs, int nsims,
 size_t force_smem_bytes(int variant);
 // alpha: tile pairs whose boxes are closer than alpha * (|c_I - c_J| + |e_I| + |e_J|)
 // take the compensated near-field path.  stats (may be null) counts near/all tile pairs.
-// Launches the far-field kernel (stream-K over all tile pairs, near ones
-// skipped) and the near-field kernel (near_acc [3][np]).
-// Far field (stream-K over tile pairs; marks near pairs in nr.bits, cleared
-// here) then the near-field work items.  5 kernels + 1 memset.
+// Launches the far field and then the near-field work items.  One-sided
+// variants: stream-K over all tile pairs, marking near pairs in nr.bits
+// (cleared here); symmetric variants: the classification kernel (near bitmap,
+// sub-block masks, fixed-point scales), then the far units in chunks from a
+// global counter.  Then the near-field count, scan and item kernels.
 // far_begin / far_end (may be null): events recorded on st around the far-field launch.
 cudaError_t launch_force_f32(const ForcePlan &p, const Staging &s, double *partial,
                              const NearScratch &nr, int *err, unsigned long long *stats,
